@@ -1,0 +1,78 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check that
+the pins of ``test_oracle_pins.py`` reject every one of them."""
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as P
+
+MUTANTS = {
+    # Eq. 1: the |m| term dropped from the exponent of the last factor
+    "drop_m_in_power": [("2.0 * nstar - (double)am - 1.0);", "2.0 * nstar - 1.0);")],
+    # Eq. 1: the cycle-averaging square root lost
+    "drop_sqrt_factor": [(
+        "omega_a * sqrt(3.0 * pow(nstar, 3.0) * E / (M_PI * pow(q, 3.0) * E_a)) *",
+        "omega_a * 1.0 *")],
+    # Eq. 1: sign of the tunnelling exponent
+    "exponent_sign": [("      exp(-expo) *", "      exp(expo) *")],
+    # Eq. 1: Q taken as the charge before ionization
+    "charge_before": [("      const double Wk = or_adk_rate(E[c], U[k], l[k], m[k], k + 1, consts);",
+                       "      const double Wk = or_adk_rate(E[c], U[k], l[k], m[k], k + 2, consts);")],
+    # Eq. 3: the rate matrix transposed (gain written above the diagonal)
+    "transposed_matrix": [("      A[(i + 1) * w + i] = Wk * dt;", "      A[i * w + (i + 1)] = Wk * dt;")],
+    # exp: diagonal reset one squaring behind
+    "stale_diagonal": [("X[i * n + i] = exp(ldexp(B[i * n + i], r));",
+                        "X[i * n + i] = exp(ldexp(B[i * n + i], r - 1));")],
+    # dn_e: electrons counted with the wrong sign (an index offset would not be
+    # a mistake: sum_k (N'_k - N_k) = 0, so sum_k (k + c)(N'_k - N_k) is the same)
+    "dne_sign": [("d += (double)(a + i) * (n1[i] - n0[i]);",
+                  "d += (double)(a + i) * (n0[i] - n1[i]);")],
+    # dn_e: the initial populations left out
+    "dne_no_initial": [("d += (double)(a + i) * (n1[i] - n0[i]);",
+                        "d += (double)(a + i) * n1[i];")],
+    # window update: slides past the top state
+    "slide_past_top": [("shifts < w - 1 && nb < Z &&", "shifts < w - 1 && nb <= Z &&")],
+}
+
+PIN_TESTS = [
+    (P.test_adk_hydrogen_closed_form, (510.0,)),
+    (P.test_adk_hydrogenic_ion_closed_form, (1500.0,)),
+    (P.test_adk_m_projection_ratio, (2, 300.0)),
+    (P.test_adk_log_slope, (1, 800.0)),
+    (P.test_expm_vs_arbitrary_precision, ([13.7, 49.7, 191.9, 142.6, 290.4],)),
+    (P.test_expm_vs_arbitrary_precision, ([2500.0, 0.2, 1e-30, 7.0],)),
+    (P.test_paper_four_level_solution, ((0.9, 2.7, 0.05),)),
+    (P.test_step_four_level_matches_paper, ()),
+    (P.test_step_single_level_closed_form, ()),
+    (P.test_window_update_rules, ()),
+]
+
+
+def run_pins(lib):
+    """Names of the pins that fail when the oracle is ``lib``."""
+    failed = []
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        for fn, args in PIN_TESTS:
+            try:
+                with np.errstate(all="ignore"):
+                    fn(*args)
+            except (AssertionError, ValueError, ZeroDivisionError, OverflowError):
+                failed.append(fn.__name__)
+            except pytest.skip.Exception:
+                pass
+    finally:
+        oracle._lib = saved
+    return failed
+
+
+def test_unmodified_oracle_passes_the_pins():
+    assert run_pins(oracle.lib()) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name):
+    lib = oracle.build_variant(MUTANTS[name], name)
+    failed = run_pins(lib)
+    assert failed, f"mutant {name} passed every pin"
