@@ -1,0 +1,405 @@
+"""Benchmark of the ionization step on GB300.
+
+Workload (default): nitrogen, 256x256x512 = 33,554,432 cells, one step of
+dt = 0.05 fs per timed iteration, FP32 populations with FP64 Bateman
+coefficients for nearly degenerate cells (ion_step, ION_F32).  Each timed
+iteration restores the pristine input state (untimed), flushes L2 (untimed),
+then times one ion_step with CUDA events on the launching stream.
+
+Printed: one JSON line with the metric (cell-updates/s), the roofline of the
+dominant kernel, the plain FP64 form on the same inputs, the end-to-end
+number through host buffers, the FP64 CPU oracle on a bounded sample, and
+the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (under torchrun) every rank runs its own full-size shard
+(weak scaling, no data-path collective); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s"
+WORKLOAD = "nitrogen_3d_256x256x512_fp32_fp64fallback"
+GRID = (256, 256, 512)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons, sampled during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        busy = sorted(sm)[len(sm) // 2:] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_oracle_sample(idx_cpu, seed=2):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload's
+    cells; returns (cell-updates/s, cells, seconds, threads, outputs)."""
+    import torch
+
+    import oracle
+    from paper_2202_10647_gb300 import workloads as W
+
+    sub = W.nitrogen_3d(*GRID, seed=seed, cells=torch.as_tensor(idx_cpu))
+    n = sub.ncells
+    osp = oracle.Species(sub.species.U, sub.species.l, sub.species.m)
+    E = sub.E.double().numpy()
+    N = sub.N[:, :n].double().numpy()
+    lo, hi = sub.lo.numpy(), sub.hi.numpy()
+    oracle.step(osp, E[:64], N[:, :64], 0.05, lo[:64], hi[:64])  # load + warm
+    t0 = time.perf_counter()
+    res = oracle.step(osp, E, N, 0.05, lo, hi)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, oracle.num_threads(), res, sub
+
+
+def sample_indices(total, n, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(total, size=min(n, total), replace=False))
+
+
+def run_reference(args):
+    """The oracle on this machine's host cores, on samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    total = GRID[0] * GRID[1] * GRID[2]
+    # size the per-step sample from a short probe so a step takes ~2-5 s
+    rate, n, dt, threads, _, _ = time_oracle_sample(sample_indices(total, 20000, 99))
+    per_step = int(min(total, max(20000, rate * 3.0)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        rate_s, n_s, dt_s, threads, _, _ = time_oracle_sample(sample_indices(total, per_step, s))
+        if s >= args.warmup:
+            times.append((n_s, dt_s))
+    cells = sum(t[0] for t in times)
+    secs = sum(t[1] for t in times)
+    value = cells / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": total, "dt_fs": 0.05,
+                   "sample_cells_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"{per_step} random cells of the {total}-cell grid per step"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_10647_gb300 import ionize
+    from paper_2202_10647_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    # -- inputs (resident in HBM before timing starts) ----------------------
+    wl = W.nitrogen_3d(*GRID, seed=2 + rank, device=dev)
+    n = wl.ncells
+    sp = ionize.Species(wl.species.U, wl.species.l, wl.species.m)
+    N0, lo0, hi0 = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
+    N, lo, hi, E = wl.N, wl.lo, wl.hi, wl.E
+    dne = torch.empty(n, dtype=torch.float32, device=dev)
+    ws = ionize.workspace(n, ionize.ION_F32, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    w = (hi0.long() - lo0.long() + 1)
+    alg_bytes = int(W.window_bytes_per_cell(lo0, hi0).sum())
+    mean_w = float(w.double().mean())
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        N.copy_(N0)
+        lo.copy_(lo0)
+        hi.copy_(hi0)
+        flush.zero_()
+
+    def timed_loop(K, Wm, fn):
+        evs = []
+        for s in range(Wm + K):
+            restore()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            if s >= Wm:
+                evs.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    def step_f32():
+        ionize.step(sp, E, N, lo, hi, 0.05, dne, ws=ws)
+
+    def step_f32_main_only():
+        ionize.step(sp, E, N, lo, hi, 0.05, dne, ws=ws, flags=ionize.ION_NO_FP64_FALLBACK)
+
+    # sampled cells for the accuracy report (inputs copied before the step)
+    idx = torch.tensor(sample_indices(n, 4000, 1), device=dev)
+
+    # -- timed region: the metric -------------------------------------------
+    timed_loop(0, args.warmup, step_f32)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_step = timed_loop(args.steps, 0, step_f32)
+        torch.cuda.synchronize()
+        t_main = timed_loop(args.steps, 0, step_f32_main_only)
+    torch.cuda.synchronize()
+    fb_cells, bad = 0, 0
+    restore()
+    step_f32()
+    torch.cuda.synchronize()
+    fb_cells, bad = ionize.counters(ws)
+    total_ms = float(sum(t_step))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms * 1e-3)
+    main_ms = float(np.mean(t_main))
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (main_ms * 1e-3) / 1e9
+
+    # -- the plain FP64 form on the same inputs ------------------------------
+    E64 = E.double()
+    N64_0 = N0.double()
+    N64 = N64_0.clone()
+    dne64 = torch.empty(n, dtype=torch.float64, device=dev)
+    ws64 = ionize.workspace(n, ionize.ION_F64_PLAIN, dev)
+
+    def step_f64():
+        ionize.step(sp, E64, N64, lo, hi, 0.05, dne64, ws=ws64, flags=ionize.ION_F64_PLAIN)
+
+    def restore64():
+        N64.copy_(N64_0)
+        lo.copy_(lo0)
+        hi.copy_(hi0)
+        flush.zero_()
+
+    k64 = max(3, min(20, args.steps // 10))
+    ev64 = []
+    for s in range(2 + k64):
+        restore64()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step_f64()
+        b.record(stream)
+        if s >= 2:
+            ev64.append((a, b))
+    torch.cuda.synchronize()
+    ms64 = float(np.mean([a.elapsed_time(b) for a, b in ev64]))
+    bytes64 = int(W.window_bytes_per_cell(lo0, hi0, elem=8).sum())
+    # FP64 vs FP32 outputs on the same inputs (one step each)
+    restore64()
+    step_f64()
+    restore()
+    step_f32()
+    torch.cuda.synchronize()
+    diff_32_64 = float((N[:, :n].double() - N64[:, :n]).abs().max())
+    del E64, N64_0, N64, dne64
+
+    # -- end to end through host buffers -------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        hE = E.cpu().pin_memory()
+        hN = N0.cpu().pin_memory()
+        hlo = lo0.cpu().pin_memory()
+        hhi = hi0.cpu().pin_memory()
+        oN = torch.empty_like(hN).pin_memory()
+        olo = torch.empty_like(hlo).pin_memory()
+        ohi = torch.empty_like(hhi).pin_memory()
+        odne = torch.empty(n, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            E.copy_(hE, non_blocking=True)
+            N.copy_(hN, non_blocking=True)
+            lo.copy_(hlo, non_blocking=True)
+            hi.copy_(hhi, non_blocking=True)
+            ionize.step(sp, E, N, lo, hi, 0.05, dne, ws=ws)
+            oN.copy_(N, non_blocking=True)
+            olo.copy_(lo, non_blocking=True)
+            ohi.copy_(hi, non_blocking=True)
+            odne.copy_(dne, non_blocking=True)
+
+        ke = max(3, min(10, args.steps // 20))
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / ke
+        h2d = hE.numel() * 4 + hN.numel() * 4 + 2 * n
+        d2h = oN.numel() * 4 + 2 * n + 4 * n
+        e2e = {"value": n / (e_ms * 1e-3), "unit": "cell-updates/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e_ms}
+        del hE, hN, oN
+
+    # -- accuracy on sampled cells and the CPU oracle baseline ---------------
+    cpu = None
+    acc = None
+    if rank == 0:
+        import oracle
+        restore()
+        Es, Ns = E[idx].double().cpu().numpy(), N[:, idx].double().cpu().numpy()
+        los, his = lo[idx].cpu().numpy(), hi[idx].cpu().numpy()
+        step_f32()
+        torch.cuda.synchronize()
+        osp = oracle.Species(wl.species.U, wl.species.l, wl.species.m)
+        No, _, _, dneo = oracle.step(osp, Es, Ns, 0.05, los, his)
+        acc = {"max_abs_err_N_vs_oracle": float(np.abs(N[:, idx].double().cpu().numpy() - No).max()),
+               "max_abs_err_dne_vs_oracle": float(np.abs(dne[idx].double().cpu().numpy() - dneo).max()),
+               "sample_cells": int(idx.numel()),
+               "max_conservation_err": float((N[:, :n].double().sum(0) - N0[:, :n].double().sum(0)).abs().max()),
+               "fp32_vs_fp64_form_max_abs": diff_32_64}
+        if not args.no_cpu_baseline:
+            total = n
+            rate, _, dtp, threads, _, _ = time_oracle_sample(sample_indices(total, 20000, 99))
+            ns = int(min(total, max(20000, rate * 12.0)))
+            rate, ns, dts, threads, _, _ = time_oracle_sample(sample_indices(total, ns, 98))
+            cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                   "sample": f"{ns} random cells of the {total}-cell grid, one step ({dts:.1f} s)"}
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "cells_per_gpu": n,
+                   "species": "N (Z=7)", "dt_fs": 0.05, "mean_window_width": mean_w,
+                   "l2": "flushed between timed steps (256 MB write) and inputs > L2",
+                   "form": "FP32 + FP64 coefficients for |W_i-W_j| < 1e-3 max(W_i,W_j)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "ion_step_f32_kernel", "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": main_ms},
+        "forms": {
+            "fp32_fp64fallback": {"value": value, "ms_per_step": ms_per_step,
+                                  "fp64_coefficient_cells": fb_cells},
+            "fp64_plain": {"value": n / (ms64 * 1e-3), "ms_per_step": ms64,
+                           "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9},
+        },
+        "accuracy": acc,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

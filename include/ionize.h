@@ -1,0 +1,173 @@
+/*
+ * ionize.h -- C ABI of the GB300 (sm_103a) multi-level tunnelling-ionization
+ * library: ADK rates and the analytic, locally reduced population update of
+ * Cheng & Samulyak, "Efficient numerical algorithm for multi-level ionization
+ * of high-atomic-number gases" (arXiv 2202.10647).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named as device arrays are caller-owned CUDA device memory of
+ *     the device that was current when the species was created.  The library
+ *     owns only the species table it allocates in ion_species_init.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Compute entry points only enqueue work on it: they allocate
+ *     nothing, never synchronize, and copy nothing between host and device,
+ *     except where a comment says otherwise.
+ *   - Return value: ION_OK (0) or a negative ION_E* code; ion_last_error()
+ *     then holds a message for the calling thread.  Arguments are checked
+ *     before anything is enqueued; a rejected call leaves every buffer as it
+ *     was.
+ *   - Populations are SoA: plane k (charge state k+, k = 0..Z) of a cell c is
+ *     N[k*ld + c].  States are numbered by charge; the rate W_k moves
+ *     population from state k to k+1 (Eq. 2), so a species with atomic number
+ *     Z has Z rates and Z+1 planes.
+ *   - Units: |E| in GV/m, dt in fs, rates in 1/fs, potentials in eV.
+ */
+#ifndef IONIZE_H
+#define IONIZE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ION_API __attribute__((visibility("default")))
+#else
+#define ION_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define ION_OK 0
+#define ION_EINVAL (-1)   /* bad argument (null, range, alignment, size)     */
+#define ION_ECUDA (-2)    /* a CUDA call or kernel launch failed              */
+#define ION_ENOMEM (-3)   /* allocation failed (species creation only)        */
+#define ION_ETIMEOUT (-4) /* a bounded device-side wait gave up               */
+
+/* ---- flags of ion_step --------------------------------------------------- */
+#define ION_F32 0x0              /* FP32 data and arithmetic; the Bateman     */
+                                 /* coefficients of cells with a nearly       */
+                                 /* degenerate rate pair are computed in FP64 */
+#define ION_F64_PLAIN 0x1        /* FP64 data (E, N, dne, n_gas are double)  */
+                                 /* and FP64 arithmetic everywhere            */
+#define ION_NO_WINDOW_UPDATE 0x2 /* keep k_lo/k_hi as given                  */
+#define ION_NO_FP64_FALLBACK 0x4 /* ION_F32 only: FP32 coefficients for all   */
+#define ION_FORCE_FP64_COEF 0x8  /* ION_F32 only: FP64 coefficients for all   */
+
+/* ---- dtype codes of ion_rates --------------------------------------------- */
+#define ION_DTYPE_F32 0
+#define ION_DTYPE_F64 1
+
+/* Largest atomic number and window width the kernels accept. */
+#define ION_MAX_Z 63
+#define ION_MAX_WINDOW 6
+
+typedef struct ion_species ion_species; /* opaque, owned by the library */
+
+/* Constants of Eq. 1.  NULL selects the printed values omega_a = 4.13e16 1/s
+ * and E_a = 510 GV/m (Sec. 2, text after Eq. 1) with U_H = 13.6 eV (U_H is
+ * named there but not given a value). */
+typedef struct {
+  double omega_a_per_s;
+  double E_a_GVm;
+  double U_H_eV;
+} ion_constants;
+
+/* Per-call policy of ion_step.  NULL selects the defaults. */
+typedef struct {
+  /* The window [lo,hi] slides up by one state while the population of its
+   * lowest state after the step is below eps_shift (the "prescribed
+   * threshold" of Sec. 3, whose value the paper does not give); default 1e-6.
+   * The window keeps its width, slides at most w-1 states per step and
+   * never past hi = Z. */
+  double eps_shift;
+  /* ION_F32: a cell whose window holds two rates with
+   * |W_i - W_j| < degen_gap * max(W_i, W_j) gets its Bateman coefficients in
+   * FP64; default 1e-3.  0 disables the test. */
+  double degen_gap;
+} ion_step_opts;
+
+/* ion_species_init -- build the per-state ADK table of one gas (Eq. 1).
+ *   U_ion_eV[k], l[k], m[k], k = 0..Z-1: ionization potential, orbital
+ *     quantum number and projection of the electron removed by W_k (host
+ *     arrays, read during the call only).  Q = k+1 is the charge after
+ *     ionization.  Requires 1 <= Z <= ION_MAX_Z, U > 0, 0 <= |m| <= l <= 20.
+ *   c: constants of Eq. 1 or NULL for the paper's values.
+ *   out: receives the handle.  The table (a few KB) is copied to the current
+ *     device synchronously; this is the only entry point that allocates.
+ * Errors: ION_EINVAL, ION_ENOMEM, ION_ECUDA. */
+ION_API int ion_species_init(const double* U_ion_eV, const int* l, const int* m, int Z,
+                     const ion_constants* c, ion_species** out);
+
+/* Frees the table.  NULL is accepted.  Must not race with work that uses it. */
+ION_API int ion_species_destroy(ion_species* sp);
+
+/* Atomic number Z of a species (or ION_EINVAL). */
+ION_API int ion_species_z(const ion_species* sp);
+
+/* ion_rates -- ADK rates W_k(|E_c|) of Eq. 1 in 1/fs for k in [k_lo, k_hi).
+ *   E: device array [ncells] of float (ION_DTYPE_F32) or double
+ *     (ION_DTYPE_F64); the magnitude |E| is used.
+ *   W_out: device array, W_k of cell c at W_out[(k-k_lo)*ldw + c], same
+ *     dtype as E; ldw >= ncells.
+ *   Requires 0 <= k_lo <= k_hi <= Z and 0 <= ncells < 2^31.
+ * W = 0 where |E| <= 1e-6 GV/m or where the tunnelling exponent
+ * (2/3)(Q/n*)^3 E_a/|E| exceeds 700. */
+ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int k_lo,
+              int k_hi, void* W_out, int64_t ldw, int dtype, void* stream);
+
+/* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
+ * a 256-byte header plus, for ION_F32, 4*ncells for the queue of cells whose
+ * coefficients are computed in FP64. */
+ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
+
+/* ion_step -- advance the charge-state populations of every cell by one
+ * step dt with the analytic solution of the window's rate equations.
+ *
+ * For each cell c with window [lo, hi] = [k_lo[c], k_hi[c]] (w = hi-lo+1
+ * states, 1 <= w <= ION_MAX_WINDOW, hi <= Z):
+ *   1. W_k = W_k(|E_c|) for k = lo..hi-1 by Eq. 1, frozen over the step
+ *      (Sec. 3, text after Eq. 3).
+ *   2. N[lo..hi] <- exp(dt A) N[lo..hi], A the [lo,hi] block of the
+ *      bidiagonal matrix of Eq. 3 with the top state absorbing (as in the
+ *      4-level system of Eqs. 6-9).  This is the sum-of-exponentials solution
+ *      of Eqs. 4-5, evaluated in Newton (divided-difference) form so that
+ *      equal and nearly equal rates need no special input.  States outside
+ *      the window are not read or written.
+ *   3. dne[c] = sum_k k (N'_k - N_k), the free electrons released per atom,
+ *      times n_gas[c] when n_gas is not NULL (overwritten, not accumulated).
+ *   4. Unless ION_NO_WINDOW_UPDATE: the window slides up (see
+ *      ion_step_opts.eps_shift; Sec. 3, text after Fig. 2 and after Eq. 9).
+ *
+ * Arguments
+ *   E      device [ncells], float (ION_F32) or double (ION_F64_PLAIN).
+ *   N      device SoA [(Z+1) * ld], same dtype; updated in place.
+ *   ld     plane stride in elements, ld >= ncells; ION_F32 needs ld % 4 == 0,
+ *          ION_F64_PLAIN ld % 2 == 0.
+ *   ncells 0 <= ncells < 2^31 (0 is a no-op).
+ *   dt_fs  0 <= dt < inf (0 leaves populations unchanged).
+ *   k_lo, k_hi  device uint8 [ncells], in/out.
+ *   dne    device [ncells], out, same dtype as E.
+ *   n_gas  device [ncells] or NULL, same dtype as E.
+ *   workspace  device, >= ion_step_workspace_bytes(ncells, flags) bytes,
+ *          256-byte aligned; its contents need no initialization.  After
+ *          the step the header holds two uint32 counters: word 0 the cells
+ *          whose coefficients were computed in FP64, word 1 the cells left
+ *          untouched because their window was invalid (lo > hi, hi > Z or
+ *          w > ION_MAX_WINDOW).
+ * Alignment: E, N, dne, n_gas 16-byte aligned; k_lo, k_hi 4-byte aligned.
+ * Calls that share a workspace must not overlap on the device.
+ * Errors: ION_EINVAL (checked before any launch), ION_ECUDA. */
+ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
+             int64_t ncells, double dt_fs, uint8_t* k_lo, uint8_t* k_hi,
+             void* dne, const void* n_gas, const ion_step_opts* opts, int flags,
+             void* workspace, size_t workspace_bytes, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+ION_API const char* ion_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IONIZE_H */

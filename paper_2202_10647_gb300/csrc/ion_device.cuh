@@ -1,0 +1,398 @@
+// ion_device.cuh -- device-side building blocks of the ionization step:
+// the species table, the ADK rate in log2 form (Eq. 1), exponential divided
+// differences, and the windowed Bateman update (Eqs. 3-9).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ionize.h"
+
+namespace ion {
+
+// ---------------------------------------------------------------------------
+// Species table.  Eq. 1 with x = E_a/|E| is W = A x^b exp(-c x), so
+//   log2 W[1/fs] = a2 - b log2|E| - C/|E|
+// with b = 2n* - |m| - 3/2, C = (2/3)(Q/n*)^3 E_a / ln 2 and
+//   a2 = log2(A) + b log2(E_a),
+//   A  = w_a sqrt(3 n*^3/(pi Q^3)) Q^2/(2 n*^2) (2e/n*)^(2n*) f(l,m)/(2 pi n*)
+//        (2 Q^3/n*^3)^(2n* - |m| - 1).
+// Built once per species on the host in double (species.cu).
+// ---------------------------------------------------------------------------
+struct SpeciesTable {
+  int Z;
+  double a2[ION_MAX_Z];
+  double b[ION_MAX_Z];
+  double C[ION_MAX_Z];
+};
+
+// Exponent (2/3)(Q/n*)^3 E_a/|E| above which W is set to 0; in the log2 units
+// of C/|E| that is 700/ln 2.
+constexpr double kCutoffLog2 = 1009.8865286222745;
+// |E| at or below which W is set to 0 (GV/m).
+constexpr double kEmin = 1e-6;
+
+// FP32 copy of the table staged in shared memory, each double held as an
+// unevaluated sum hi + lo of two floats, with log2(dt) folded into a.
+struct StagedF32 {
+  float a_hi[ION_MAX_Z + 1], a_lo[ION_MAX_Z + 1];
+  float b_hi[ION_MAX_Z + 1], b_lo[ION_MAX_Z + 1];
+  float C_hi[ION_MAX_Z + 1], C_lo[ION_MAX_Z + 1];
+};
+
+struct StagedF64 {
+  double a[ION_MAX_Z + 1];  // a2 + log2(dt)
+  double b[ION_MAX_Z + 1];
+  double C[ION_MAX_Z + 1];
+};
+
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = isfinite(x) ? __double2float_rn(x - (double)hi) : 0.0f;
+}
+
+// Threads [0, Z) of the block stage the table; the caller syncs.
+__device__ __forceinline__ void stage_f32(const SpeciesTable* t, double log2dt,
+                                          StagedF32* s) {
+  const int Z = t->Z;
+  for (int k = threadIdx.x; k < Z; k += blockDim.x) {
+    split_f64(t->a2[k] + log2dt, s->a_hi[k], s->a_lo[k]);
+    split_f64(t->b[k], s->b_hi[k], s->b_lo[k]);
+    split_f64(t->C[k], s->C_hi[k], s->C_lo[k]);
+  }
+}
+
+__device__ __forceinline__ void stage_f64(const SpeciesTable* t, double log2dt,
+                                          StagedF64* s) {
+  const int Z = t->Z;
+  for (int k = threadIdx.x; k < Z; k += blockDim.x) {
+    s->a[k] = t->a2[k] + log2dt;
+    s->b[k] = t->b[k];
+    s->C[k] = t->C[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rate times dt in FP32 with float-float exponent arithmetic.  The exponent
+// y = a - b log2|E| - C/|E| is a sum of terms of size up to ~10^3 whose
+// result matters to ~1e-7 absolute (relative error of W*dt), so the large
+// terms are carried as hi+lo pairs (Dekker/Knuth two-sum and fma two-product).
+// ---------------------------------------------------------------------------
+struct FieldF32 {
+  float E, rE;   // |E| and 1/|E|
+  float ex, lm;  // log2|E| = ex + lm, ex integer, lm in [0,1)
+  bool zero;     // W = 0 for every state
+};
+
+__device__ __forceinline__ FieldF32 field_f32(float E_in) {
+  FieldF32 f;
+  float E = fabsf(E_in);
+  f.zero = !(E > (float)kEmin) || isinf(E);
+  E = f.zero ? 1.0f : E;
+  int e2;
+  const float mant = frexpf(E, &e2);  // E = mant 2^e2, mant in [0.5, 1)
+  f.lm = log2f(mant * 2.0f);
+  f.ex = (float)(e2 - 1);
+  f.E = E;
+  f.rE = __frcp_rn(E);
+  return f;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float rate_dt_f32(const StagedF32& t, int k,
+                                             const FieldF32& f) {
+  if (f.zero) return 0.0f;
+  const float Ch = t.C_hi[k];
+  const float q = Ch * f.rE;
+  if (q > (float)kCutoffLog2) return 0.0f;
+  const float ql = (fmaf(-q, f.E, Ch) + t.C_lo[k]) * f.rE;  // C/E = q + ql
+  const float bh = t.b_hi[k];
+  const float p = bh * f.ex;
+  const float pe = fmaf(bh, f.ex, -p);  // b_hi*ex = p + pe exactly
+  float s1, e1, s2, e2;
+  two_sum(t.a_hi[k], -p, s1, e1);
+  two_sum(s1, -q, s2, e2);
+  const float small =
+      ((t.a_lo[k] - pe) - ql) - fmaf(bh, f.lm, t.b_lo[k] * (f.ex + f.lm));
+  float y = s2 + ((e1 + e2) + small);
+  y = fminf(y, 99.0f);  // W dt <= 2^99: keeps every later product finite
+  return exp2f(y);
+}
+
+__device__ __forceinline__ double rate_dt_f64(const StagedF64& t, int k,
+                                              double E_in) {
+  const double E = fabs(E_in);
+  if (!(E > kEmin) || isinf(E)) return 0.0;
+  const double q = t.C[k] / E;
+  if (q > kCutoffLog2) return 0.0;
+  double y = t.a[k] - t.b[k] * log2(E) - q;
+  y = fmin(y, 1000.0);
+  return exp2(y);
+}
+
+// ---------------------------------------------------------------------------
+// Divided differences of exp.
+//
+// For nodes z_0..z_{NR-1} (z = -W dt) the Bateman coefficient of Eqs. 4-5
+// that carries population from state j to state i > j is
+//   P_ij = (prod_{q=j}^{i-1} W_q dt) * exp[z_j, ..., z_i],
+// exp[...] the divided difference of exp on those nodes; P_ii = e^{z_i}.
+// For distinct rates this is the sum of exponentials of Eq. 4 (Eqs. 6-8 for
+// four levels); written as a divided difference it stays defined and
+// accurate for equal and nearly equal rates.
+//
+// dd_exp_all fills D[mask] = exp[{z_k : bit k of mask}] for every non-empty
+// subset, smallest subsets first:
+//   * spread s = max z - min z of the subset >= TAU: the two-term recurrence
+//     that removes the subset's smallest and its largest node,
+//       D(S) = (D(S \ {argmin}) - D(S \ {argmax})) / s.
+//     Dividing by the full spread bounds the cancellation (both terms are
+//     positive and the divisor is the largest gap in S).
+//   * s < TAU: the Taylor series of the divided difference about the
+//     largest node z*,
+//       exp[S] = e^{z*} sum_{r>=0} h_r(z - z*) / (|S|-1+r)!,
+//     h_r the complete homogeneous symmetric polynomial of degree r,
+//     truncated at the first R with s^(R+1)/(R+1)! below the target.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DDParams;
+
+template <>
+struct DDParams<float> {
+  static constexpr float tau = 1.0f;
+  static constexpr int RMAX = 11;
+  __device__ static __forceinline__ int terms(float s) {
+    // s^(R+1)/(R+1)! < 3e-9
+    int R = 11;
+    R = s <= 0.824531f ? 10 : R;
+    R = s <= 0.636339f ? 9 : R;
+    R = s <= 0.46856f ? 8 : R;
+    R = s <= 0.32384f ? 7 : R;
+    R = s <= 0.204816f ? 6 : R;
+    R = s <= 0.113695f ? 5 : R;
+    R = s <= 0.0514352f ? 4 : R;
+    R = s <= 0.0163807f ? 3 : R;
+    R = s <= 0.00262074f ? 2 : R;
+    R = s <= 7.74597e-05f ? 1 : R;
+    return R;
+  }
+};
+
+template <>
+struct DDParams<double> {
+  static constexpr double tau = 0.25;
+  static constexpr int RMAX = 12;
+  __device__ static __forceinline__ int terms(double s) {
+    // s^(R+1)/(R+1)! < 2e-17
+    int R = 12;
+    R = s <= 0.214675 ? 11 : R;
+    R = s <= 0.148911 ? 10 : R;
+    R = s <= 0.0968455 ? 9 : R;
+    R = s <= 0.0578509 ? 8 : R;
+    R = s <= 0.0307836 ? 7 : R;
+    R = s <= 0.0139108 ? 6 : R;
+    R = s <= 0.00493242 ? 5 : R;
+    R = s <= 0.00119136 ? 4 : R;
+    R = s <= 0.000148017 ? 3 : R;
+    R = s <= 4.93242e-06 ? 2 : R;
+    R = s <= 6.32456e-09 ? 1 : R;
+    return R;
+  }
+};
+
+
+__host__ __device__ constexpr int popc_c(int x) {
+  return x == 0 ? 0 : (x & 1) + popc_c(x >> 1);
+}
+
+__host__ __device__ constexpr int ctz_c(int x) {
+  return (x & 1) ? 0 : 1 + ctz_c(x >> 1);
+}
+
+// mask of the contiguous node range [j, i]
+__host__ __device__ constexpr int range_mask(int j, int i) {
+  return ((1 << (i + 1)) - 1) & ~((1 << j) - 1);
+}
+
+// 1/n! for n = 0..17 (the Taylor branch needs n <= 4 + 12).
+__device__ constexpr double kInvFact[18] = {
+    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040,
+    1.0 / 40320, 1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600,
+    1.0 / 6227020800.0, 1.0 / 87178291200.0, 1.0 / 1307674368000.0,
+    1.0 / 20922789888000.0, 1.0 / 355687428096000.0};
+
+// Taylor branch of dd_exp_all for the subset `mask` of the nodes z[0..n-1]
+// (n <= 5), without the factor e^{zmx}: sum_r h_r(z - zmx) / (m-1+r)!.
+// Kept out of line: it is the rare branch, and one copy per precision keeps
+// the kernels small.
+template <typename T>
+__device__ __noinline__ T dd_taylor(T z0, T z1, T z2, T z3, T z4, int mask,
+                                    T zmx, T s) {
+  using P = DDParams<T>;
+  const int R = P::terms(s);
+  const T zz[5] = {z0, z1, z2, z3, z4};
+  T H[P::RMAX + 1];
+  H[0] = T(1);
+#pragma unroll
+  for (int r = 1; r <= P::RMAX; ++r) H[r] = T(0);
+  int m = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (!((mask >> k) & 1)) continue;
+    ++m;
+    const T x = zz[k] - zmx;
+#pragma unroll
+    for (int r = 1; r <= P::RMAX; ++r)
+      if (r <= R) H[r] = fma(x, H[r - 1], H[r]);
+  }
+  T acc = T(0);
+#pragma unroll
+  for (int r = 0; r <= P::RMAX; ++r)
+    if (r <= R) acc = fma(H[r], T(kInvFact[m - 1 + r]), acc);
+  return acc;
+}
+
+template <typename T, int NR>
+__device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
+                                           T (&D)[1 << NR]) {
+  using P = DDParams<T>;
+  D[0] = T(0);
+#pragma unroll
+  for (int mask = 1; mask < (1 << NR); ++mask) {
+    if (popc_c(mask) == 1) {
+      D[mask] = ez[ctz_c(mask)];
+      continue;
+    }
+    T zmn = T(0), zmx = T(0), emx = T(0), dmin = T(0), dmax = T(0);
+    bool first = true;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      if (!((mask >> k) & 1)) continue;
+      const T zk = z[k];
+      const T dk = D[mask ^ (1 << k)];
+      if (first) {
+        zmn = zk;
+        zmx = zk;
+        emx = ez[k];
+        dmin = dk;
+        dmax = dk;
+        first = false;
+      } else {
+        const bool lo = zk < zmn, hi = zk > zmx;
+        zmn = lo ? zk : zmn;
+        dmin = lo ? dk : dmin;
+        zmx = hi ? zk : zmx;
+        emx = hi ? ez[k] : emx;
+        dmax = hi ? dk : dmax;
+      }
+    }
+    const T s = zmx - zmn;
+    T d;
+    if (s >= P::tau) {
+      d = (dmin - dmax) / s;
+    } else {
+      d = emx * dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
+                             NR > 2 ? z[NR > 2 ? 2 : 0] : T(0),
+                             NR > 3 ? z[NR > 3 ? 3 : 0] : T(0),
+                             NR > 4 ? z[NR > 4 ? 4 : 0] : T(0), mask, zmx, s);
+    }
+    D[mask] = d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Windowed update of one cell (Eqs. 3-9).
+//   v[0..w-1]  populations of the window states lo..hi (in), N' (out);
+//              entries r >= w are left alone.
+//   lam[r]     W_{lo+r} dt for r < w-1 (entries r >= w-1 are ignored).
+//   WM         compile-time bound on w (2 <= w <= WM).
+// Rows r < w-1 use the divided-difference coefficients; the absorbing top
+// state gets what the others lost, so the window's sum is kept (Eq. 9 is
+// 1 - Eqs. 6-8 column by column).  Returns the electrons released,
+// sum_k k (N'_k - N_k) = sum over the w-1 internal boundaries of the
+// population that crossed them.
+// ---------------------------------------------------------------------------
+template <typename T, int WM>
+__device__ __forceinline__ T window_update(T (&v)[WM], const T (&lam)[WM],
+                                           int w) {
+  constexpr int NR = WM - 1;
+  T z[NR], ez[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const T l = r < w - 1 ? lam[r] : T(0);
+    z[r] = -l;
+    ez[r] = exp(-l);
+  }
+  T D[1 << NR];
+  dd_exp_all<T, NR>(z, ez, D);
+  T out[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    T acc = T(0), prod = T(1);
+#pragma unroll
+    for (int j = i; j >= 0; --j) {
+      if (j < i) prod *= (j < w - 1 ? lam[j] : T(0));
+      acc = fma(prod * D[range_mask(j, i)], v[j], acc);
+    }
+    out[i] = acc;
+  }
+  // electrons: flux across boundary b (between b and b+1) is S_b - S'_b
+  T S = T(0), S1 = T(0), dne = T(0), tot = T(0), lost = T(0);
+#pragma unroll
+  for (int r = 0; r < WM; ++r) tot += r < w ? v[r] : T(0);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r < w - 1) {
+      S += v[r];
+      S1 += out[r];
+      dne += S - S1;
+      lost += out[r];
+    }
+  }
+  const T top = tot - lost;
+#pragma unroll
+  for (int r = 0; r < WM; ++r) {
+    if (r < w - 1)
+      v[r] = out[r];
+    else if (r == w - 1)
+      v[r] = top;
+  }
+  return dne;
+}
+
+// North-star degeneracy test: some pair of the window's rates with
+// |W_i - W_j| < gap * max(W_i, W_j).
+template <typename T, int WM>
+__device__ __forceinline__ bool near_degenerate(const T (&lam)[WM], int w,
+                                                T gap) {
+  bool deg = false;
+#pragma unroll
+  for (int i = 0; i < WM - 1; ++i)
+#pragma unroll
+    for (int j = i + 1; j < WM - 1; ++j)
+      if (j < w - 1)
+        deg |= fabs(lam[i] - lam[j]) < gap * fmax(lam[i], lam[j]);
+  return deg;
+}
+
+// Window slide after the step (Sec. 3): while the lowest state holds less
+// than eps and the top is below Z, move the window up one state, at most
+// w-1 times.  lo/hi are updated in place.
+template <typename T, int WM>
+__device__ __forceinline__ void slide_window(const T (&v)[WM], int w, int Z,
+                                             T eps, int& lo, int& hi) {
+  bool go = true;
+#pragma unroll
+  for (int r = 0; r < WM - 1; ++r) {
+    go = go && (r < w - 1) && (hi < Z) && (v[r] < eps);
+    lo += go ? 1 : 0;
+    hi += go ? 1 : 0;
+  }
+}
+
+}  // namespace ion

@@ -1,0 +1,41 @@
+// ion_step.cuh -- launch arguments shared by the step kernels and the host
+// launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ion_device.cuh"
+
+namespace ion {
+
+// Workspace header (uint32 words at the start of the workspace).
+constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
+constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
+constexpr size_t kHdrBytes = 256;
+
+struct StepArgs {
+  const SpeciesTable* tab;
+  int Z;
+  const void* E;
+  void* N;
+  int64_t ld;
+  int ncells;
+  double log2dt;
+  int zero_dt;
+  uint8_t* lo;
+  uint8_t* hi;
+  void* dne;
+  const void* n_gas;
+  double eps;
+  double gap;
+  int flags;
+  uint32_t* hdr;
+  uint32_t* queue;
+};
+
+// Launchers (step.cu).  They only enqueue; the caller has validated.
+cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_step_f64(const StepArgs& a, cudaStream_t s);
+
+}  // namespace ion

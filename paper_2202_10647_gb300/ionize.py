@@ -1,0 +1,234 @@
+"""Thin Python binding of libionize.so (include/ionize.h).
+
+Argument marshalling only: every function takes torch tensors, checks their
+dtype/device/shape, and passes raw device pointers and the current CUDA
+stream to the C ABI.  All arithmetic runs in the library's CUDA kernels.
+There is no CPU path: without the library or a GPU these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+ION_OK = 0
+ION_EINVAL = -1
+ION_ECUDA = -2
+ION_ENOMEM = -3
+ION_ETIMEOUT = -4
+
+ION_F32 = 0x0
+ION_F64_PLAIN = 0x1
+ION_NO_WINDOW_UPDATE = 0x2
+ION_NO_FP64_FALLBACK = 0x4
+ION_FORCE_FP64_COEF = 0x8
+
+ION_DTYPE_F32 = 0
+ION_DTYPE_F64 = 1
+
+ION_MAX_Z = 63
+ION_MAX_WINDOW = 6
+
+#: every symbol include/ionize.h declares
+EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
+           "ion_rates", "ion_step_workspace_bytes", "ion_step", "ion_last_error")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class IonError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ionize error {code}: {msg}")
+        self.code = code
+
+
+class _Constants(ctypes.Structure):
+    _fields_ = [("omega_a_per_s", ctypes.c_double), ("E_a_GVm", ctypes.c_double),
+                ("U_H_eV", ctypes.c_double)]
+
+
+class _StepOpts(ctypes.Structure):
+    _fields_ = [("eps_shift", ctypes.c_double), ("degen_gap", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def _declare(lib):
+    lib.ion_last_error.restype = ctypes.c_char_p
+    lib.ion_last_error.argtypes = []
+    lib.ion_species_init.restype = ctypes.c_int
+    lib.ion_species_init.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                     ctypes.POINTER(_Constants), ctypes.POINTER(_vp)]
+    lib.ion_species_destroy.restype = ctypes.c_int
+    lib.ion_species_destroy.argtypes = [_vp]
+    lib.ion_species_z.restype = ctypes.c_int
+    lib.ion_species_z.argtypes = [_vp]
+    lib.ion_rates.restype = ctypes.c_int
+    lib.ion_rates.argtypes = [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, _vp, _i64,
+                              ctypes.c_int, _vp]
+    lib.ion_step_workspace_bytes.restype = ctypes.c_size_t
+    lib.ion_step_workspace_bytes.argtypes = [_i64, ctypes.c_int]
+    lib.ion_step.restype = ctypes.c_int
+    lib.ion_step.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
+                             _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp,
+                             ctypes.c_size_t, _vp]
+    return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libionize.so (compiling it first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"{path} is missing; run __graft_entry__.build()")
+                _build.build()
+            _lib = _declare(ctypes.CDLL(path))
+    return _lib
+
+
+def _check(rc: int):
+    if rc != ION_OK:
+        raise IonError(rc, lib().ion_last_error().decode())
+
+
+def _stream(t: torch.Tensor):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, name: str, dtype, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Species:
+    """ADK table of one gas (ion_species_init).  U, l, m are sequences of
+    length Z for the Z ionizing transitions k -> k+1."""
+
+    def __init__(self, U, l, m, constants=None):
+        U = [float(x) for x in U]
+        l = [int(x) for x in l]
+        m = [int(x) for x in m]
+        Z = len(U)
+        if len(l) != Z or len(m) != Z:
+            raise ValueError("U, l and m must have the same length")
+        self.Z = Z
+        self.U, self.l, self.m = U, l, m
+        Ua = (ctypes.c_double * Z)(*U)
+        la = (ctypes.c_int * Z)(*l)
+        ma = (ctypes.c_int * Z)(*m)
+        c = None
+        if constants is not None:
+            c = ctypes.byref(_Constants(*[float(x) for x in constants]))
+        h = _vp()
+        _check(lib().ion_species_init(Ua, la, ma, Z, c, ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ion_species_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rates(sp: Species, E: torch.Tensor, k_lo: int, k_hi: int,
+          out: torch.Tensor | None = None) -> torch.Tensor:
+    """W_k(|E|) in 1/fs for k in [k_lo, k_hi): tensor (k_hi-k_lo, ncells)."""
+    if E.dtype not in (torch.float32, torch.float64):
+        raise ValueError("E must be float32 or float64")
+    _need(E, "E", E.dtype)
+    n = E.numel()
+    if out is None:
+        out = torch.empty((k_hi - k_lo, n), dtype=E.dtype, device=E.device)
+    _need(out, "out", E.dtype, E.device)
+    ldw = out.shape[1] if out.dim() == 2 else n
+    dtype = ION_DTYPE_F32 if E.dtype == torch.float32 else ION_DTYPE_F64
+    _check(lib().ion_rates(sp.handle, _ptr(E), n, int(k_lo), int(k_hi), _ptr(out),
+                           ldw, dtype, _stream(E)))
+    return out
+
+
+def workspace_bytes(ncells: int, flags: int = ION_F32) -> int:
+    return int(lib().ion_step_workspace_bytes(int(ncells), int(flags)))
+
+
+def workspace(ncells: int, flags: int = ION_F32, device=None) -> torch.Tensor:
+    """A device buffer big enough for ion_step (256-byte aligned by torch)."""
+    nb = workspace_bytes(ncells, flags)
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def step(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
+         k_hi: torch.Tensor, dt: float, dne: torch.Tensor,
+         n_gas: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+         eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32,
+         ncells: int | None = None) -> torch.Tensor:
+    """One ion_step.  N is (Z+1, ld) and is updated in place, as are k_lo and
+    k_hi; dne is written.  Returns the workspace (its header holds the
+    counters described in include/ionize.h)."""
+    f64 = bool(flags & ION_F64_PLAIN)
+    dt_ = torch.float64 if f64 else torch.float32
+    _need(E, "E", dt_)
+    dev = E.device
+    _need(N, "N", dt_, dev)
+    _need(k_lo, "k_lo", torch.uint8, dev)
+    _need(k_hi, "k_hi", torch.uint8, dev)
+    _need(dne, "dne", dt_, dev)
+    if n_gas is not None:
+        _need(n_gas, "n_gas", dt_, dev)
+    if N.dim() != 2 or N.shape[0] != sp.Z + 1:
+        raise ValueError(f"N must have shape (Z+1, ld) = ({sp.Z + 1}, ld)")
+    n = E.numel() if ncells is None else int(ncells)
+    if ws is None:
+        ws = workspace(n, flags, dev)
+    _need(ws, "ws", torch.uint8, dev)
+    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    _check(lib().ion_step(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
+                          _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
+                          ctypes.byref(opts), int(flags), _ptr(ws), ws.numel(),
+                          _stream(E)))
+    return ws
+
+
+def counters(ws: torch.Tensor):
+    """(cells done with FP64 coefficients, cells skipped for invalid windows)
+    of the last step that used `ws` (synchronizes)."""
+    h = ws[:8].cpu().view(torch.int32)
+    return int(h[0]), int(h[1])

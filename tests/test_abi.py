@@ -1,0 +1,64 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports
+every symbol include/ionize.h declares, and rejects bad arguments on the host
+before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2202_10647_gb300 import build as B
+from paper_2202_10647_gb300 import ionize
+
+HEADER = os.path.join(B.INCLUDE, "ionize.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"ION_API\s+[\w\s\*]+?\b(ion_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_symbols() == sorted(ionize.EXPORTS)
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_sm_103a():
+    r = __import__("subprocess").run(
+        ["cuobjdump", "--list-elf", B.LIB], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in r.stdout
+
+
+def test_host_side_rejections():
+    lib = ionize.lib()
+    d = (ctypes.c_double * 3)(10.0, 20.0, 30.0)
+    i3 = (ctypes.c_int * 3)(0, 1, 0)
+    m_bad = (ctypes.c_int * 3)(0, 2, 0)   # |m| > l
+    h = ctypes.c_void_p()
+    assert lib.ion_species_init(d, i3, i3, 0, None, ctypes.byref(h)) == ionize.ION_EINVAL
+    assert lib.ion_species_init(d, i3, i3, 64, None, ctypes.byref(h)) == ionize.ION_EINVAL
+    assert lib.ion_species_init(d, i3, m_bad, 3, None, ctypes.byref(h)) == ionize.ION_EINVAL
+    assert b"m" in lib.ion_last_error()
+    neg = (ctypes.c_double * 3)(10.0, -1.0, 30.0)
+    assert lib.ion_species_init(neg, i3, i3, 3, None, ctypes.byref(h)) == ionize.ION_EINVAL
+    assert lib.ion_species_init(d, i3, i3, 3, None, None) == ionize.ION_EINVAL
+    # NULL species is rejected before anything else
+    assert lib.ion_step(None, None, None, 0, 0, 0.05, None, None, None, None, None, 0,
+                        None, 0, None) == ionize.ION_EINVAL
+    assert lib.ion_rates(None, None, 0, 0, 0, None, 0, 0, None) == ionize.ION_EINVAL
+    assert lib.ion_species_z(None) == ionize.ION_EINVAL
+    assert lib.ion_species_destroy(None) == ionize.ION_OK
+
+
+def test_workspace_sizes():
+    assert ionize.workspace_bytes(0) == 256
+    assert ionize.workspace_bytes(1000) == 256 + 4000
+    assert ionize.workspace_bytes(1000, ionize.ION_F64_PLAIN) == 256

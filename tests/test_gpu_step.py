@@ -1,0 +1,370 @@
+"""Parity of the CUDA step with the FP64 oracle, through the C ABI.
+
+Tolerances (per cell, per population, Sigma_k N_k = 1):
+  FP32 form          |N - N_oracle| <= 2e-6, |dne - dne_oracle| <= (w-1) 2e-6
+  plain FP64 form    |N - N_oracle| <= 1e-12, |dne - dne_oracle| <= 1e-11
+Inputs are identical on both sides: the oracle gets the GPU's fp32 inputs
+promoted to double.  Window decisions are compared exactly except for cells
+whose lowest-state population lies within the tolerance of eps_shift.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2202_10647_gb300 import ionize, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ionize.ION_F32: 2e-6, ionize.ION_F64_PLAIN: 1e-12}
+
+
+def gpu_species(sd):
+    return ionize.Species(sd.U, sd.l, sd.m)
+
+
+def oracle_species(sd):
+    return oracle.Species(sd.U, sd.l, sd.m)
+
+
+def run_both(sd, E, N, lo, hi, dt=0.05, flags=ionize.ION_F32, n=None, eps=1e-6,
+             gap=1e-3, update=True, n_gas=None):
+    """Run one GPU step and the oracle on the same inputs.  E (float32 [n]),
+    N (float32 [Z+1, ld]), lo/hi (uint8) are CPU tensors."""
+    n = E.numel() if n is None else n
+    f64 = bool(flags & ionize.ION_F64_PLAIN)
+    dt_ = torch.float64 if f64 else torch.float32
+    dev = torch.device("cuda")
+    sp = gpu_species(sd)
+    Eg = E.to(dt_).to(dev)
+    Ng = N.to(dt_).to(dev)
+    log, hig = lo.clone().to(dev), hi.clone().to(dev)
+    dne = torch.full((max(n, 1),), float("nan"), dtype=dt_, device=dev)
+    ng = None if n_gas is None else n_gas.to(dt_).to(dev)
+    upd = 0 if update else ionize.ION_NO_WINDOW_UPDATE
+    ws = ionize.step(sp, Eg, Ng, log, hig, dt, dne, n_gas=ng, eps_shift=eps,
+                     degen_gap=gap, flags=flags | upd, ncells=n)
+    torch.cuda.synchronize()
+    out = dict(N=Ng.double().cpu().numpy(), lo=log.cpu().numpy(), hi=hig.cpu().numpy(),
+               dne=dne[:n].double().cpu().numpy(), counters=ionize.counters(ws))
+    # the oracle sees exactly the values the GPU read
+    Ein = E.to(dt_).double().numpy()[:n]
+    Nin = N.to(dt_).double().numpy()[:, :n]
+    No, loo, hio, dneo = oracle.step(oracle_species(sd), Ein, Nin, dt, lo.numpy()[:n],
+                                     hi.numpy()[:n], None if n_gas is None else
+                                     n_gas.to(dt_).double().numpy()[:n],
+                                     eps_shift=eps, window_update=update)
+    ref = dict(N=No, lo=loo, hi=hio, dne=dneo)
+    return out, ref
+
+
+def check(out, ref, lo, hi, flags, eps=1e-6, n=None):
+    tol = TOL[flags & ionize.ION_F64_PLAIN]
+    n = ref["N"].shape[1] if n is None else n
+    Ng = out["N"][:, :n]
+    err = np.abs(Ng - ref["N"]).max(axis=0)
+    assert err.max() <= tol, f"max |N - oracle| = {err.max():g} at cell {err.argmax()}"
+    w = hi.numpy()[:n].astype(int) - lo.numpy()[:n].astype(int) + 1
+    derr = np.abs(out["dne"] - ref["dne"])
+    dtol = np.maximum(w - 1, 1) * tol * 5
+    assert np.all(derr <= dtol), f"max |dne - oracle| = {derr.max():g}"
+    # windows: exact, except where the lowest states sit within tol of eps
+    tie = np.zeros(n, bool)
+    for c in np.nonzero((out["lo"][:n] != ref["lo"]) | (out["hi"][:n] != ref["hi"]))[0]:
+        a = int(lo[c])
+        vals = ref["N"][a:a + w[c] - 1, c]
+        tie[c] = np.any(np.abs(vals - eps) <= 2 * tol)
+    bad = ((out["lo"][:n] != ref["lo"]) | (out["hi"][:n] != ref["hi"])) & ~tie
+    assert not bad.any(), f"{bad.sum()} window decisions differ"
+
+
+def cells_of(wl, n=None):
+    n = wl.ncells if n is None else n
+    return wl.E[:n], wl.N, wl.lo[:n], wl.hi[:n]
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("flags", [ionize.ION_F32, ionize.ION_F64_PLAIN])
+def test_nitrogen_grid_parity(flags):
+    wl = W.nitrogen_3d(16, 32, 64, seed=11)
+    n = wl.ncells - 3  # ragged tail: not a multiple of the 4 cells per thread
+    E, N, lo, hi = cells_of(wl, n)
+    out, ref = run_both(wl.species, E, N, lo, hi, flags=flags, n=n)
+    check(out, ref, lo, hi, flags, n=n)
+    # planes past the last cell are untouched
+    assert np.array_equal(out["N"][:, n:], wl.N[:, n:].double().numpy())
+
+
+@pytest.mark.parametrize("flags", [ionize.ION_F32 | ionize.ION_NO_FP64_FALLBACK,
+                                   ionize.ION_F32 | ionize.ION_FORCE_FP64_COEF])
+def test_fp32_coefficient_modes(flags):
+    wl = W.nitrogen_3d(8, 32, 64, seed=12)
+    E, N, lo, hi = cells_of(wl)
+    out, ref = run_both(wl.species, E, N, lo, hi, flags=flags)
+    check(out, ref, lo, hi, ionize.ION_F32)
+    fb, bad = out["counters"]
+    assert bad == 0
+    if flags & ionize.ION_FORCE_FP64_COEF:
+        w = (hi.long() - lo.long() + 1)
+        assert fb == int((w >= 2).sum())
+    else:
+        assert fb == 0
+
+
+@pytest.mark.parametrize("name", ["Ar-like", "Kr-like"])
+@pytest.mark.parametrize("flags", [ionize.ION_F32, ionize.ION_F64_PLAIN])
+def test_ladder_parity(name, flags):
+    sd = W.argon_like() if name == "Ar-like" else W.krypton_like()
+    wl = W.ladder_cells(sd, 20000, seed=21, block=64)
+    E, N, lo, hi = cells_of(wl)
+    out, ref = run_both(sd, E, N, lo, hi, flags=flags)
+    check(out, ref, lo, hi, flags)
+
+
+def adversarial(sd, seed=0):
+    """Every window width 1..6 at the bottom, middle and top of the ladder
+    against fields from 0 to 1e6 GV/m, plus fields at which two rates of a
+    window cross (equal and nearly equal rates)."""
+    Z = sd.Z
+    Es = [0.0, 1e-7, 1e-3, 1.0, 30.0, 100.0, 300.0, 700.0, 1000.0, 2000.0, 4000.0,
+          6000.0, 1e4, 1e5, 1e6]
+    # crossings of W_i and W_j for i < j in the same 6-wide window
+    osp = oracle_species(sd)
+    grid = np.exp(np.linspace(math.log(20), math.log(2e4), 4000))
+    Wg = np.log(np.maximum(oracle.rates(osp, grid, 0, Z), 1e-300))
+    for i in range(Z):
+        for j in range(i + 1, min(Z, i + 5)):
+            d = Wg[i] - Wg[j]
+            ok = (Wg[i] > -200) & (Wg[j] > -200)
+            s = np.nonzero((np.sign(d[:-1]) != np.sign(d[1:])) & ok[:-1])[0]
+            for t in s[:2]:
+                a, b = grid[t], grid[t + 1]
+                for _ in range(60):
+                    c = math.sqrt(a * b)
+                    dc = (math.log(max(oracle.adk_rate(c, sd.U[i], sd.l[i], sd.m[i], i + 1), 1e-300))
+                          - math.log(max(oracle.adk_rate(c, sd.U[j], sd.l[j], sd.m[j], j + 1), 1e-300)))
+                    if np.sign(dc) == np.sign(d[t]):
+                        a = c
+                    else:
+                        b = c
+                for rel in (0.0, 1e-9, 1e-6, 1e-4, 1e-3, 3e-3, 1e-2, 0.1):
+                    Es.append(float(np.float32(a * (1 + rel))))
+    E, lo, hi = [], [], []
+    for e in Es:
+        for w in range(1, 7):
+            for base in sorted({0, Z // 3, Z // 2, Z + 1 - w}):
+                if base + w - 1 > Z or base < 0:
+                    continue
+                E.append(e)
+                lo.append(base)
+                hi.append(base + w - 1)
+    n = len(E)
+    ld = (n + 3) // 4 * 4
+    lo_t = torch.tensor(lo, dtype=torch.uint8)
+    p = torch.tensor([h - l + 1 for l, h in zip(lo, hi)])
+    N = W.populations(seed, lo_t, p, Z, ld)
+    return torch.tensor(E, dtype=torch.float32), N, lo_t, torch.tensor(hi, dtype=torch.uint8)
+
+
+@pytest.mark.parametrize("name", ["N", "Ar-like", "Kr-like"])
+@pytest.mark.parametrize("flags", [ionize.ION_F32, ionize.ION_F32 | ionize.ION_NO_FP64_FALLBACK,
+                                   ionize.ION_F64_PLAIN])
+def test_adversarial_cells(name, flags):
+    sd = {"N": W.nitrogen(), "Ar-like": W.argon_like(), "Kr-like": W.krypton_like()}[name]
+    E, N, lo, hi = adversarial(sd)
+    out, ref = run_both(sd, E, N, lo, hi, flags=flags)
+    check(out, ref, lo, hi, flags)
+    assert np.all(np.isfinite(out["N"]))
+    tot_in = N.double().numpy().sum(0)[:E.numel()]
+    tot_out = out["N"].sum(0)[:E.numel()]
+    assert np.abs(tot_out - tot_in).max() <= (1e-6 if not flags & 1 else 1e-14)
+
+
+@pytest.mark.parametrize("dt", [0.0, 1e-4, 0.05, 1.0])
+def test_time_steps_and_gas_density(dt):
+    wl = W.nitrogen_3d(8, 16, 32, seed=13)
+    E, N, lo, hi = cells_of(wl)
+    ng = 1.0 + torch.arange(wl.ncells, dtype=torch.float32) % 7
+    for flags in (ionize.ION_F32, ionize.ION_F64_PLAIN):
+        out, ref = run_both(wl.species, E, N, lo, hi, dt=dt, flags=flags, n_gas=ng)
+        check(out, ref, lo, hi, flags)
+        if dt == 0.0:
+            assert np.array_equal(out["N"], N.to(torch.float64 if flags else torch.float32).double().numpy())
+            assert np.all(out["dne"] == 0.0)
+
+
+def test_invalid_windows_are_skipped_and_counted():
+    sd = W.nitrogen()
+    E = torch.full((8,), 1500.0)
+    lo = torch.tensor([0, 3, 5, 2, 0, 1, 4, 6], dtype=torch.uint8)
+    hi = torch.tensor([3, 2, 9, 8, 6, 4, 7, 7], dtype=torch.uint8)  # 1: lo>hi, 2: hi>Z, 3,4: w>6
+    N = W.populations(1, lo.clamp(max=7), torch.full((8,), 2), 7, 8)
+    dev = "cuda"
+    sp = gpu_species(sd)
+    Ng = N.to(dev)
+    log, hig = lo.to(dev), hi.to(dev)
+    dne = torch.full((8,), -7.0, device=dev)
+    ws = ionize.step(sp, E.to(dev), Ng, log, hig, 0.05, dne)
+    fb, bad = ionize.counters(ws)
+    assert bad == 4
+    for c in (1, 2, 3, 4):
+        assert torch.equal(Ng[:, c].cpu(), N[:, c])
+        assert float(dne[c]) == -7.0
+        assert int(log[c]) == int(lo[c]) and int(hig[c]) == int(hi[c])
+    assert float(dne[0]) != -7.0
+
+
+def test_guard_planes_untouched():
+    """Canaries: planes and cells around the arrays stay bit-identical."""
+    wl = W.nitrogen_3d(8, 16, 32, seed=14)
+    n = wl.ncells
+    dev = "cuda"
+    Z = 7
+    guard = 64
+    big = torch.full((Z + 3, n + 2 * guard), 12345.0, device=dev)
+    big[1:Z + 2, guard:guard + n] = wl.N[:, :n].to(dev)
+    # view with ld = n + 2*guard starting at plane 1, cell `guard`
+    N = big[1:Z + 2]
+    sp = gpu_species(wl.species)
+    E = torch.full((n + 2 * guard,), 777.0, device=dev)
+    E[guard:guard + n] = wl.E.to(dev)
+    lo = torch.full((n + 2 * guard,), 200, dtype=torch.uint8, device=dev)
+    hi = lo.clone()
+    lo[guard:guard + n] = wl.lo.to(dev)
+    hi[guard:guard + n] = wl.hi.to(dev)
+    dne = torch.full((n + 2 * guard,), 5.5, device=dev)
+    lib = ionize.lib()
+    ws = ionize.workspace(n)
+    import ctypes
+    off = guard
+    rc = lib.ion_step(sp.handle, ctypes.c_void_p(E.data_ptr() + 4 * off),
+                      ctypes.c_void_p(N.data_ptr() + 4 * off), N.shape[1], n, 0.05,
+                      ctypes.c_void_p(lo.data_ptr() + off), ctypes.c_void_p(hi.data_ptr() + off),
+                      ctypes.c_void_p(dne.data_ptr() + 4 * off), None, None, 0,
+                      ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.ion_last_error()
+    torch.cuda.synchronize()
+    b = big.cpu()
+    assert torch.all(b[0] == 12345.0) and torch.all(b[Z + 2] == 12345.0)
+    assert torch.all(b[:, :guard] == 12345.0) and torch.all(b[:, guard + n:] == 12345.0)
+    d = dne.cpu()
+    assert torch.all(d[:guard] == 5.5) and torch.all(d[guard + n:] == 5.5)
+    assert torch.all(lo.cpu()[:guard] == 200) and torch.all(lo.cpu()[guard + n:] == 200)
+
+
+def test_argument_validation():
+    sd = W.nitrogen()
+    sp = gpu_species(sd)
+    dev = "cuda"
+    n = 64
+    E = torch.full((n,), 100.0, device=dev)
+    N = torch.zeros((8, n), device=dev)
+    lo = torch.zeros(n, dtype=torch.uint8, device=dev)
+    hi = torch.full((n,), 3, dtype=torch.uint8, device=dev)
+    dne = torch.empty(n, device=dev)
+    ws = ionize.workspace(n)
+    ok = dict(sp=sp, E=E, N=N, k_lo=lo, k_hi=hi, dt=0.05, dne=dne, ws=ws)
+    ionize.step(**ok)
+    bad = [dict(dt=-1.0), dict(dt=float("inf")), dict(ws=ws[:100]), dict(eps_shift=-1.0),
+           dict(degen_gap=1.5), dict(flags=0x100),
+           dict(flags=ionize.ION_NO_FP64_FALLBACK | ionize.ION_FORCE_FP64_COEF)]
+    for b in bad:
+        args = dict(ok)
+        args.update(b)
+        with pytest.raises(ionize.IonError) as ei:
+            ionize.step(**args)
+        assert ei.value.code == ionize.ION_EINVAL
+    # misaligned E (offset by one float) and ld not a multiple of 4
+    import ctypes
+    lib = ionize.lib()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.ion_step(sp.handle, ctypes.c_void_p(E.data_ptr() + 4), ctypes.c_void_p(N.data_ptr()),
+                      n, n - 1, 0.05, ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
+                      ctypes.c_void_p(dne.data_ptr()), None, None, 0, ctypes.c_void_p(ws.data_ptr()),
+                      ws.numel(), st)
+    assert rc == ionize.ION_EINVAL
+    rc = lib.ion_step(sp.handle, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(N.data_ptr()),
+                      n - 2, n - 2, 0.05, ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
+                      ctypes.c_void_p(dne.data_ptr()), None, None, 0, ctypes.c_void_p(ws.data_ptr()),
+                      ws.numel(), st)
+    assert rc == ionize.ION_EINVAL
+    # empty input is a no-op
+    ionize.step(sp, E[:0], N, lo[:0], hi[:0], 0.05, dne[:0], ws=ws, ncells=0)
+
+
+@pytest.mark.parametrize("dtype,rtol", [(torch.float32, 2e-6), (torch.float64, 1e-12)])
+def test_rates_parity(dtype, rtol):
+    for sd in (W.nitrogen(), W.argon_like(), W.krypton_like()):
+        E = torch.tensor(np.exp(np.linspace(math.log(1e-7), math.log(2e5), 3001)), dtype=dtype)
+        E[0] = 0.0
+        sp = gpu_species(sd)
+        Wg = ionize.rates(sp, E.cuda(), 0, sd.Z).double().cpu().numpy()
+        Wo = oracle.rates(oracle_species(sd), E.double().numpy(), 0, sd.Z)
+        big = Wo * 0.05 > 1e-30
+        rel = np.abs(Wg[big] - Wo[big]) / Wo[big]
+        assert rel.max() <= rtol, rel.max()
+        # where the oracle says 0 the GPU agrees, up to values no step can see
+        assert np.all(Wg[Wo == 0] * 0.05 <= 1e-30)
+        assert np.all(np.abs(Wg[~big]) * 0.05 <= 2e-30)
+
+
+def test_nitrogen_pulse_200_steps_fp64():
+    """The 2D nitrogen run: 200 steps of 0.05 fs from N_0 = 1, window [0,3],
+    with window updates; FP64 parity at every step."""
+    sd = W.nitrogen()
+    wl = W.nitrogen_2d_initial()
+    n = wl.ncells
+    dev = "cuda"
+    sp = gpu_species(sd)
+    osp = oracle_species(sd)
+    N = wl.N.double().to(dev)
+    lo, hi = wl.lo.clone().to(dev), wl.hi.clone().to(dev)
+    dne = torch.empty(n, dtype=torch.float64, device=dev)
+    ws = ionize.workspace(n, ionize.ION_F64_PLAIN)
+    No = wl.N[:, :n].double().numpy()
+    loo, hio = wl.lo.numpy().copy(), wl.hi.numpy().copy()
+    worst = 0.0
+    for s in range(200):
+        E = W.nitrogen_pulse_2d(s * 0.05)
+        ionize.step(sp, E.double().to(dev), N, lo, hi, 0.05, dne, ws=ws,
+                    flags=ionize.ION_F64_PLAIN)
+        No, loo, hio, dneo = oracle.step(osp, E.double().numpy(), No, 0.05, loo, hio)
+        if s % 10 == 9 or s == 199:
+            Ng = N[:, :n].cpu().numpy()
+            worst = max(worst, float(np.abs(Ng - No).max()))
+            assert worst <= 1e-12, (s, worst)
+            assert np.array_equal(lo.cpu().numpy(), loo) and np.array_equal(hi.cpu().numpy(), hio)
+            assert np.abs(dne.cpu().numpy() - dneo).max() <= 1e-11
+    # something happened: the front ionized at least the first two levels
+    assert float(N[0, :n].min()) < 1e-3
+
+
+def test_full_size_nitrogen_sampled():
+    """The 256x256x512 nitrogen workload as the benchmark runs it: sampled
+    cells against the oracle, and properties over every cell."""
+    dev = "cuda"
+    wl = W.nitrogen_3d(device=dev)
+    n = wl.ncells
+    rng = np.random.default_rng(0)
+    idx = torch.tensor(np.sort(rng.choice(n, 20000, replace=False)), device=dev)
+    E_s, N_s = wl.E[idx].cpu(), wl.N[:, idx].cpu()
+    lo_s, hi_s = wl.lo[idx].cpu(), wl.hi[idx].cpu()
+    tot0 = wl.N[:, :n].double().sum(0)
+    sp = gpu_species(wl.species)
+    dne = torch.empty(n, device=dev)
+    ws = ionize.step(sp, wl.E, wl.N, wl.lo, wl.hi, 0.05, dne)
+    torch.cuda.synchronize()
+    fb, bad = ionize.counters(ws)
+    assert bad == 0 and fb < n // 50
+    tot1 = wl.N[:, :n].double().sum(0)
+    assert float((tot1 - tot0).abs().max()) <= 1e-6
+    assert float(wl.N[:, :n].min()) >= -1e-6
+    assert bool(torch.all(wl.hi <= 7)) and bool(torch.all(wl.lo <= wl.hi))
+    No, loo, hio, dneo = oracle.step(oracle_species(wl.species), E_s.double().numpy(),
+                                     N_s.double().numpy(), 0.05, lo_s.numpy(), hi_s.numpy())
+    Ng = wl.N[:, idx].double().cpu().numpy()
+    assert np.abs(Ng - No).max() <= 2e-6
+    assert np.abs(dne[idx].double().cpu().numpy() - dneo).max() <= 1e-5
