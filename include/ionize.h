@@ -53,7 +53,8 @@ extern "C" {
                                  /* and FP64 arithmetic everywhere            */
 #define ION_NO_WINDOW_UPDATE 0x2 /* keep k_lo/k_hi as given                  */
 #define ION_NO_FP64_FALLBACK 0x4 /* ION_F32 only: FP32 coefficients for all   */
-#define ION_FORCE_FP64_COEF 0x8  /* ION_F32 only: FP64 coefficients for all   */
+#define ION_FORCE_FP64_COEF 0x8  /* ION_F32 only: FP64 coefficients for every */
+                                 /* cell that takes the Bateman form          */
 
 /* ---- dtype codes of ion_rates --------------------------------------------- */
 #define ION_DTYPE_F32 0
@@ -118,8 +119,9 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
               int k_hi, void* W_out, int64_t ldw, int dtype, void* stream);
 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
- * a 256-byte header plus, for ION_F32, 4*ncells for the queue of cells whose
- * coefficients are computed in FP64. */
+ * a 256-byte header plus, for ION_F32, two queues: one 4-byte slot per cell
+ * (cells whose coefficients are computed in FP64) and one per 32-cell chunk
+ * (chunks holding a window of 5 or 6 states, finished by a second kernel). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
 
 /* ion_step -- advance the charge-state populations of every cell by one
@@ -132,9 +134,12 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *   2. N[lo..hi] <- exp(dt A) N[lo..hi], A the [lo,hi] block of the
  *      bidiagonal matrix of Eq. 3 with the top state absorbing (as in the
  *      4-level system of Eqs. 6-9).  This is the sum-of-exponentials solution
- *      of Eqs. 4-5, evaluated in Newton (divided-difference) form so that
- *      equal and nearly equal rates need no special input.  States outside
- *      the window are not read or written.
+ *      of Eqs. 4-5 ("the Bateman form"), evaluated in Newton
+ *      (divided-difference) form so that equal and nearly equal rates need
+ *      no special input; a cell whose rates all have W dt <= 1 (FP32) or
+ *      <= 1/2 (FP64) takes the Taylor series of exp(dt A) instead, which
+ *      reaches the same result with fewer operations.  States outside the
+ *      window are not read or written.
  *   3. dne[c] = sum_k k (N'_k - N_k), the free electrons released per atom,
  *      times n_gas[c] when n_gas is not NULL (overwritten, not accumulated).
  *   4. Unless ION_NO_WINDOW_UPDATE: the window slides up (see
@@ -143,8 +148,7 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  * Arguments
  *   E      device [ncells], float (ION_F32) or double (ION_F64_PLAIN).
  *   N      device SoA [(Z+1) * ld], same dtype; updated in place.
- *   ld     plane stride in elements, ld >= ncells; ION_F32 needs ld % 4 == 0,
- *          ION_F64_PLAIN ld % 2 == 0.
+ *   ld     plane stride in elements, ld >= ncells.
  *   ncells 0 <= ncells < 2^31 (0 is a no-op).
  *   dt_fs  0 <= dt < inf (0 leaves populations unchanged).
  *   k_lo, k_hi  device uint8 [ncells], in/out.
@@ -152,11 +156,12 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *   n_gas  device [ncells] or NULL, same dtype as E.
  *   workspace  device, >= ion_step_workspace_bytes(ncells, flags) bytes,
  *          256-byte aligned; its contents need no initialization.  After
- *          the step the header holds two uint32 counters: word 0 the cells
+ *          the step the header holds uint32 counters: word 0 the cells
  *          whose coefficients were computed in FP64, word 1 the cells left
  *          untouched because their window was invalid (lo > hi, hi > Z or
- *          w > ION_MAX_WINDOW).
- * Alignment: E, N, dne, n_gas 16-byte aligned; k_lo, k_hi 4-byte aligned.
+ *          w > ION_MAX_WINDOW), word 2 the 32-cell chunks done by the
+ *          wide-window kernel.
+ * Alignment: E, N, dne, n_gas aligned to their element size.
  * Calls that share a workspace must not overlap on the device.
  * Errors: ION_EINVAL (checked before any launch), ION_ECUDA. */
 ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,

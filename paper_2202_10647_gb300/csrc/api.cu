@@ -88,9 +88,9 @@ __global__ void rates_f32_kernel(const ion::SpeciesTable* t, const float* E,
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
-  const ion::FieldF32 f = ion::field_f32(E[c]);
+  const ion::FieldF32 f = ion::field_f32<true>(E[c]);
   for (int k = k_lo; k < k_hi; ++k)
-    W[(int64_t)(k - k_lo) * ldw + c] = ion::rate_dt_f32(tab, k, f);
+    W[(int64_t)(k - k_lo) * ldw + c] = ion::rate_dt_f32<true>(tab, k, f);
 }
 
 __global__ void rates_f64_kernel(const ion::SpeciesTable* t, const double* E,
@@ -205,8 +205,7 @@ int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int k_lo,
 
 size_t ion_step_workspace_bytes(int64_t ncells, int flags) {
   if (ncells < 0) ncells = 0;
-  if (flags & ION_F64_PLAIN) return ion::kHdrBytes;
-  return ion::kHdrBytes + 4 * (size_t)ncells;
+  return ion::step_workspace_bytes(ncells, (flags & ION_F64_PLAIN) != 0);
 }
 
 int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
@@ -242,14 +241,11 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
     if (!E || !N || !k_lo || !k_hi || !dne)
       return fail(ION_EINVAL, "E, N, k_lo, k_hi and dne must be non-NULL");
     if (ld < ncells) return fail(ION_EINVAL, "ld=%lld < ncells", (long long)ld);
-    const int vec = f64 ? 2 : 4;
-    if (ld % vec) return fail(ION_EINVAL, "ld must be a multiple of %d", vec);
     if (ld > (int64_t(1) << 40)) return fail(ION_EINVAL, "ld too large");
-    if (!aligned(E, 16) || !aligned(N, 16) || !aligned(dne, 16) ||
-        (n_gas && !aligned(n_gas, 16)))
-      return fail(ION_EINVAL, "E, N, dne and n_gas must be 16-byte aligned");
-    if (!aligned(k_lo, 4) || !aligned(k_hi, 4))
-      return fail(ION_EINVAL, "k_lo and k_hi must be 4-byte aligned");
+    const size_t el = f64 ? 8 : 4;
+    if (!aligned(E, el) || !aligned(N, el) || !aligned(dne, el) ||
+        (n_gas && !aligned(n_gas, el)))
+      return fail(ION_EINVAL, "E, N, dne and n_gas must be aligned to their element size");
   }
   ion::StepArgs a;
   a.tab = sp->dev;
@@ -267,8 +263,7 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
   a.eps = o.eps_shift;
   a.gap = o.degen_gap;
   a.flags = flags;
-  a.hdr = static_cast<uint32_t*>(workspace);
-  a.queue = reinterpret_cast<uint32_t*>(static_cast<char*>(workspace) + ion::kHdrBytes);
+  ion::bind_workspace(a, workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = f64 ? ion::launch_step_f64(a, s) : ion::launch_step_f32(a, sp->num_sms, s);
   return e == cudaSuccess ? ok() : cuda_fail(e, "ion_step launch");

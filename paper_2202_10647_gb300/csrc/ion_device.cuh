@@ -79,22 +79,26 @@ __device__ __forceinline__ void stage_f64(const SpeciesTable* t, double log2dt,
 // terms are carried as hi+lo pairs (Dekker/Knuth two-sum and fma two-product).
 // ---------------------------------------------------------------------------
 struct FieldF32 {
-  float E, rE;   // |E| and 1/|E|
+  float E, rE;   // |E| and an approximation of 1/|E| (its error is corrected)
   float ex, lm;  // log2|E| = ex + lm, ex integer, lm in [0,1)
+  float lg;      // ex + lm rounded to float
   bool zero;     // W = 0 for every state
 };
 
+template <bool Precise = false>
 __device__ __forceinline__ FieldF32 field_f32(float E_in) {
   FieldF32 f;
   float E = fabsf(E_in);
   f.zero = !(E > (float)kEmin) || isinf(E);
   E = f.zero ? 1.0f : E;
-  int e2;
-  const float mant = frexpf(E, &e2);  // E = mant 2^e2, mant in [0.5, 1)
-  f.lm = log2f(mant * 2.0f);
-  f.ex = (float)(e2 - 1);
+  // E is normal here: split the exponent and the mantissa in [1, 2)
+  const int bits = __float_as_int(E);
+  const float mant = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+  f.ex = (float)((bits >> 23) - 127);
+  f.lm = Precise ? log2f(mant) : __log2f(mant);
+  f.lg = f.ex + f.lm;
   f.E = E;
-  f.rE = __frcp_rn(E);
+  f.rE = Precise ? __frcp_rn(E) : __fdividef(1.0f, E);
   return f;
 }
 
@@ -104,22 +108,38 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// y = a - b log2|E| - C/|E| (log2 of W dt).  A plain FP32 evaluation first;
+// where it says W dt < 2^-12 its error (below 2^-10 relative for terms up
+// to 10^3) moves W dt by less than 3e-7 and no population can see it, so
+// only larger rates take the float-float evaluation.
+template <bool Precise = false>
 __device__ __forceinline__ float rate_dt_f32(const StagedF32& t, int k,
                                              const FieldF32& f) {
   if (f.zero) return 0.0f;
   const float Ch = t.C_hi[k];
   const float q = Ch * f.rE;
   if (q > (float)kCutoffLog2) return 0.0f;
-  const float ql = (fmaf(-q, f.E, Ch) + t.C_lo[k]) * f.rE;  // C/E = q + ql
   const float bh = t.b_hi[k];
+  if (!Precise) {
+    const float y0 = fmaf(-bh, f.lg, t.a_hi[k]) - q;
+    if (y0 < -12.0f) return exp2f(y0);
+  }
+  const float ql = (fmaf(-q, f.E, Ch) + t.C_lo[k]) * f.rE;  // C/E = q + ql
   const float p = bh * f.ex;
   const float pe = fmaf(bh, f.ex, -p);  // b_hi*ex = p + pe exactly
   float s1, e1, s2, e2;
   two_sum(t.a_hi[k], -p, s1, e1);
   two_sum(s1, -q, s2, e2);
   const float small =
-      ((t.a_lo[k] - pe) - ql) - fmaf(bh, f.lm, t.b_lo[k] * (f.ex + f.lm));
-  float y = s2 + ((e1 + e2) + small);
+      ((t.a_lo[k] - pe) - ql) - fmaf(bh, f.lm, t.b_lo[k] * f.lg);
+  const float tail = (e1 + e2) + small;
+  if (Precise) {
+    // 2^(s2 + tail) as 2^s2 2^tail keeps the relative error at a few ulp for
+    // any size of the exponent (rounding s2 + tail to one float would cost
+    // up to |y| 2^-24 relative).
+    return s2 > 99.0f ? exp2f(99.0f) : exp2f(s2) * exp2f(tail);
+  }
+  float y = s2 + tail;
   y = fminf(y, 99.0f);  // W dt <= 2^99: keeps every later product finite
   return exp2f(y);
 }
@@ -159,52 +179,53 @@ __device__ __forceinline__ double rate_dt_f64(const StagedF64& t, int k,
 //     h_r the complete homogeneous symmetric polynomial of degree r,
 //     truncated at the first R with s^(R+1)/(R+1)! below the target.
 // ---------------------------------------------------------------------------
+// Number of Taylor terms: the smallest R with x^(R+1)/(R+1)! below the
+// target (3e-9 in FP32, 2e-17 in FP64), i.e. the number of thresholds
+// kThr[i] = (target (i+1)!)^(1/(i+1)) that lie below x.
+__device__ constexpr float kThrF32[17] = {
+    3e-09f,    7.74597e-05f, 0.00262074f, 0.0163807f, 0.0514352f, 0.113695f,
+    0.204816f, 0.32384f,     0.46856f,    0.636339f,  0.824531f,  1.03067f,
+    1.25256f,  1.48827f,     1.7361f,     1.99461f,   2.26256f};
+__device__ constexpr double kThrF64[20] = {
+    2e-17,     6.32456e-09, 4.93242e-06, 0.000148017, 0.00119136, 0.00493242,
+    0.0139108, 0.0307836,   0.0578509,   0.0968455,   0.148911,   0.214675,
+    0.294354,  0.387859,    0.494882,    0.614969,    0.747572,   0.892092,
+    1.04791,   1.21439};
+
 template <typename T>
 struct DDParams;
 
 template <>
 struct DDParams<float> {
-  static constexpr float tau = 1.0f;
-  static constexpr int RMAX = 11;
-  __device__ static __forceinline__ int terms(float s) {
-    // s^(R+1)/(R+1)! < 3e-9
-    int R = 11;
-    R = s <= 0.824531f ? 10 : R;
-    R = s <= 0.636339f ? 9 : R;
-    R = s <= 0.46856f ? 8 : R;
-    R = s <= 0.32384f ? 7 : R;
-    R = s <= 0.204816f ? 6 : R;
-    R = s <= 0.113695f ? 5 : R;
-    R = s <= 0.0514352f ? 4 : R;
-    R = s <= 0.0163807f ? 3 : R;
-    R = s <= 0.00262074f ? 2 : R;
-    R = s <= 7.74597e-05f ? 1 : R;
+  static constexpr float tau = 1.0f;   // Taylor below this subset spread
+  static constexpr int RMAX = 11;      // terms needed at spread tau
+  static constexpr float prop_max = 1.0f;  // Taylor propagation up to max W dt
+  static constexpr int PMAX = 16;      // terms needed at 2 * prop_max
+  __device__ static __forceinline__ int terms(float x, int rmax) {
+    int R = 0;
+#pragma unroll
+    for (int i = 0; i < 17; ++i)
+      if (i < rmax) R += x > kThrF32[i] ? 1 : 0;
     return R;
   }
+  __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
 };
 
 template <>
 struct DDParams<double> {
   static constexpr double tau = 0.25;
   static constexpr int RMAX = 12;
-  __device__ static __forceinline__ int terms(double s) {
-    // s^(R+1)/(R+1)! < 2e-17
-    int R = 12;
-    R = s <= 0.214675 ? 11 : R;
-    R = s <= 0.148911 ? 10 : R;
-    R = s <= 0.0968455 ? 9 : R;
-    R = s <= 0.0578509 ? 8 : R;
-    R = s <= 0.0307836 ? 7 : R;
-    R = s <= 0.0139108 ? 6 : R;
-    R = s <= 0.00493242 ? 5 : R;
-    R = s <= 0.00119136 ? 4 : R;
-    R = s <= 0.000148017 ? 3 : R;
-    R = s <= 4.93242e-06 ? 2 : R;
-    R = s <= 6.32456e-09 ? 1 : R;
+  static constexpr double prop_max = 0.5;
+  static constexpr int PMAX = 18;
+  __device__ static __forceinline__ int terms(double x, int rmax) {
+    int R = 0;
+#pragma unroll
+    for (int i = 0; i < 20; ++i)
+      if (i < rmax) R += x > kThrF64[i] ? 1 : 0;
     return R;
   }
+  __device__ static __forceinline__ double div(double a, double b) { return a / b; }
 };
-
 
 __host__ __device__ constexpr int popc_c(int x) {
   return x == 0 ? 0 : (x & 1) + popc_c(x >> 1);
@@ -234,7 +255,7 @@ template <typename T>
 __device__ __noinline__ T dd_taylor(T z0, T z1, T z2, T z3, T z4, int mask,
                                     T zmx, T s) {
   using P = DDParams<T>;
-  const int R = P::terms(s);
+  const int R = P::terms(s, P::RMAX);
   const T zz[5] = {z0, z1, z2, z3, z4};
   T H[P::RMAX + 1];
   H[0] = T(1);
@@ -294,7 +315,7 @@ __device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
     const T s = zmx - zmn;
     T d;
     if (s >= P::tau) {
-      d = (dmin - dmax) / s;
+      d = P::div(dmin - dmax, s);
     } else {
       d = emx * dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
                              NR > 2 ? z[NR > 2 ? 2 : 0] : T(0),
@@ -305,21 +326,62 @@ __device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
   }
 }
 
+// Small rates: N' = sum_k (dt A)^k N / k! applied to the window vector
+// directly.  With every W dt <= prop_max the norm of dt A is at most
+// 2 prop_max, the terms shrink from the first, and R terms leave a remainder
+// below (2 prop_max)^(R+1)/(R+1)!.  inc[] collects N' - N without forming
+// the difference, so the freed electrons carry no cancellation.
+//   v, lam, w as in dd_update below; returns the electrons released.
+template <typename T, int WM>
+__device__ __forceinline__ T taylor_propagate(T (&v)[WM], const T (&lam)[WM],
+                                              int w, T lmax) {
+  using P = DDParams<T>;
+  const int R = P::terms(T(2) * lmax, P::PMAX);
+  T t[WM], inc[WM];
+#pragma unroll
+  for (int i = 0; i < WM; ++i) {
+    t[i] = i < w ? v[i] : T(0);
+    inc[i] = T(0);
+  }
+#pragma unroll
+  for (int k = 1; k <= P::PMAX; ++k) {
+    if (k > R) break;
+    const T rk = T(1.0 / k);
+#pragma unroll
+    for (int i = WM - 1; i >= 0; --i) {
+      const T gain = i > 0 ? lam[i - 1] * t[i - 1] : T(0);
+      t[i] = (gain - lam[i] * t[i]) * rk;
+      inc[i] += t[i];
+    }
+  }
+  T cum = T(0), dne = T(0);
+#pragma unroll
+  for (int r = 0; r < WM; ++r) {
+    if (r < w - 1) {
+      cum -= inc[r];  // population that left states <= r
+      dne += cum;
+    }
+    if (r < w) v[r] += inc[r];
+  }
+  return dne;
+}
+
 // ---------------------------------------------------------------------------
-// Windowed update of one cell (Eqs. 3-9).
+// Windowed update of one cell (Eqs. 3-9) with the divided-difference
+// (Bateman) coefficients.
 //   v[0..w-1]  populations of the window states lo..hi (in), N' (out);
 //              entries r >= w are left alone.
-//   lam[r]     W_{lo+r} dt for r < w-1 (entries r >= w-1 are ignored).
+//   lam[r]     W_{lo+r} dt for r < w-1; lam[r] = 0 for r >= w-1 (the top
+//              state of the window absorbs, as in Eqs. 6-9).
 //   WM         compile-time bound on w (2 <= w <= WM).
-// Rows r < w-1 use the divided-difference coefficients; the absorbing top
-// state gets what the others lost, so the window's sum is kept (Eq. 9 is
-// 1 - Eqs. 6-8 column by column).  Returns the electrons released,
-// sum_k k (N'_k - N_k) = sum over the w-1 internal boundaries of the
-// population that crossed them.
+// Rows r < w-1 use the coefficients; the absorbing top state gets what the
+// others lost, so the window's sum is kept (Eq. 9 is 1 - Eqs. 6-8 column by
+// column).  Returns the electrons released, sum_k k (N'_k - N_k) = the sum
+// over the w-1 internal boundaries of the population that crossed them.
+// (Cells whose rates are all small take taylor_propagate instead.)
 // ---------------------------------------------------------------------------
 template <typename T, int WM>
-__device__ __forceinline__ T window_update(T (&v)[WM], const T (&lam)[WM],
-                                           int w) {
+__device__ __forceinline__ T dd_update(T (&v)[WM], const T (&lam)[WM], int w) {
   constexpr int NR = WM - 1;
   T z[NR], ez[NR];
 #pragma unroll

@@ -12,6 +12,8 @@ namespace ion {
 // Workspace header (uint32 words at the start of the workspace).
 constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
 constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
+constexpr int kHdrWide = 2;      // 32-cell chunks queued for the wide kernel
+constexpr int kHdrWords = 3;
 constexpr size_t kHdrBytes = 256;
 
 struct StepArgs {
@@ -30,9 +32,14 @@ struct StepArgs {
   double eps;
   double gap;
   int flags;
-  uint32_t* hdr;
-  uint32_t* queue;
+  uint32_t* hdr;    // workspace header (kHdr* words)
+  uint32_t* queue;  // cells for the FP64-coefficient kernel
+  uint32_t* wide;   // first cell of each 32-cell chunk for the wide kernel
 };
+
+// Workspace layout (step.cu).
+size_t step_workspace_bytes(int64_t ncells, bool f64);
+void bind_workspace(StepArgs& a, void* ws);
 
 // Launchers (step.cu).  They only enqueue; the caller has validated.
 cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s);

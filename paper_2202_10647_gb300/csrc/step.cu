@@ -1,14 +1,18 @@
 // step.cu -- the ion_step kernels.
 //
-//   ion_step_f32_kernel   FP32 SoA, 4 cells per thread (16-byte vector
-//                         loads/stores of every window plane when the 4
-//                         cells share their window), one window-width bucket
-//                         per warp, FP32 rates and coefficients.  Cells with
-//                         a nearly degenerate rate pair are left untouched
-//                         and queued in the workspace.
+// FP32 form (ION_F32), three kernels on the caller's stream:
+//   ion_step_f32_kernel   one cell per thread over all cells.  A warp whose
+//                         32 cells all have windows of <= 4 states finishes
+//                         them here; a warp holding a wider window is queued
+//                         whole (one entry per 32-cell chunk) so that the
+//                         wide code paths do not set this kernel's register
+//                         budget.  Cells with a nearly degenerate rate pair
+//                         are left untouched and queued one by one.
+//   ion_step_f32_wide_kernel   the queued 32-cell chunks (windows of 5-6).
 //   ion_step_fb_kernel    the queued cells: the same FP32 rates, FP64
 //                         Bateman coefficients and propagation, rounded back.
-//   ion_step_f64_kernel   the plain FP64 form, 2 cells per thread.
+// Plain FP64 form (ION_F64_PLAIN): ion_step_f64_kernel, one cell per thread,
+// every width inline.
 //
 // One step is Eqs. 1-9 of the paper per cell; see ion_device.cuh.
 #include <cstdint>
@@ -27,78 +31,14 @@ __device__ __forceinline__ bool window_ok(int lo, int hi, int Z) {
   return lo <= hi && hi <= Z && hi - lo + 1 <= ION_MAX_WINDOW;
 }
 
-// Append the flagged cells of a warp to the FP64 queue with one atomic per
-// warp.  Every lane of the warp calls this.
-template <int CPT>
-__device__ __forceinline__ void queue_append(const StepArgs& a,
-                                             const bool (&fb)[CPT], int c0) {
-  int nf = 0;
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) nf += fb[j] ? 1 : 0;
-  if (!__ballot_sync(kFull, nf > 0)) return;
-  const int lane = threadIdx.x & 31;
-  int x = nf;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, x, o);
-    x += lane >= o ? y : 0;
-  }
-  const int total = __shfl_sync(kFull, x, 31);
-  unsigned base = 0;
-  if (lane == 31) base = atomicAdd(&a.hdr[kHdrFallback], (unsigned)total);
-  base = __shfl_sync(kFull, base, 31);
-  unsigned pos = base + (unsigned)(x - nf);
-#pragma unroll
-  for (int j = 0; j < CPT; ++j)
-    if (fb[j]) a.queue[pos++] = (uint32_t)(c0 + j);
-}
-
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using type = float4;
-  static constexpr int n = 4;
-};
-template <>
-struct Vec16<double> {
-  using type = double2;
-  static constexpr int n = 2;
-};
-
-template <typename T>
-__device__ __forceinline__ void unpack(const typename Vec16<T>::type& x,
-                                       T (&o)[Vec16<T>::n]);
-template <>
-__device__ __forceinline__ void unpack<float>(const float4& x, float (&o)[4]) {
-  o[0] = x.x;
-  o[1] = x.y;
-  o[2] = x.z;
-  o[3] = x.w;
-}
-template <>
-__device__ __forceinline__ void unpack<double>(const double2& x,
-                                               double (&o)[2]) {
-  o[0] = x.x;
-  o[1] = x.y;
-}
-__device__ __forceinline__ float4 pack(const float (&o)[4]) {
-  return make_float4(o[0], o[1], o[2], o[3]);
-}
-__device__ __forceinline__ double2 pack(const double (&o)[2]) {
-  return make_double2(o[0], o[1]);
-}
-
-// Per-precision hooks of the generic cell loop.
+// Per-precision hooks of the generic cell code.
 struct F32Form {
   using T = float;
   using Staged = StagedF32;
-  struct Field {
-    FieldF32 f;
-  };
-  __device__ static Field field(float E) { return {field_f32(E)}; }
+  using Field = FieldF32;
+  __device__ static Field field(float E) { return field_f32(E); }
   __device__ static float rate(const StagedF32& t, int k, const Field& f) {
-    return rate_dt_f32(t, k, f.f);
+    return rate_dt_f32(t, k, f);
   }
 };
 
@@ -114,262 +54,148 @@ struct F64Form {
   }
 };
 
+// Warp-aggregated append of `value` for the lanes with `take` set: one
+// atomic per warp.  Every lane of the warp calls this.
+__device__ __forceinline__ void warp_append(uint32_t* counter, uint32_t* queue,
+                                            bool take, uint32_t value) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(counter, (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, 0);
+  if (take) queue[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
 // ---------------------------------------------------------------------------
-// The CPT cells c0..c0+CPT-1 of one thread, window width bound WM.
-// lo/hi are the cells' windows (in), nlo/nhi the windows after the slide
-// (out).  fb[j] is set for cells left to the FP64 queue.
+// One cell (index c, window [lo, hi] of width w <= WM, validated).
+// Returns true if the cell was left to the FP64 queue.
 // ---------------------------------------------------------------------------
-template <class F, int WM, int CPT>
-__device__ __forceinline__ void cells(const StepArgs& a,
-                                      const typename F::Staged& tab, int c0,
-                                      bool full, const typename F::T (&Ev)[CPT],
-                                      const int (&lo)[CPT], const int (&hi)[CPT],
-                                      const bool (&ok)[CPT], int (&nlo)[CPT],
-                                      int (&nhi)[CPT], bool (&fb)[CPT],
-                                      typename F::T (&dne)[CPT], bool allow_fb) {
+template <class F, int WM>
+__device__ __forceinline__ bool cell(const StepArgs& a,
+                                     const typename F::Staged& tab, int c,
+                                     typename F::T Ec, int lo, int hi,
+                                     bool allow_fb) {
   using T = typename F::T;
-  using V = Vec16<T>;
   T* __restrict__ N = static_cast<T*>(a.N);
   const int64_t ld = a.ld;
-  int w[CPT];
-  bool uni = full;
+  const int w = hi - lo + 1;
+  T v[WM];
 #pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    w[j] = ok[j] ? hi[j] - lo[j] + 1 : 0;
-    uni = uni && ok[j] && lo[j] == lo[0] && w[j] == w[0];
-  }
+  for (int r = 0; r < WM; ++r)
+    v[r] = r < w ? __ldcs(N + (int64_t)(lo + r) * ld + c) : T(0);
 
-  T v[CPT][WM];
+  T dne = T(0);
+  int nlo = lo, nhi = hi;
+  if constexpr (WM >= 2) {
+   if (w >= 2) {
+    const typename F::Field f = F::field(Ec);
+    T lam[WM];
+    T lmax = T(0);
 #pragma unroll
-  for (int j = 0; j < CPT; ++j)
-#pragma unroll
-    for (int r = 0; r < WM; ++r) v[j][r] = T(0);
-  if (uni) {
-#pragma unroll
-    for (int r = 0; r < WM; ++r)
-      if (r < w[0]) {
-        T o[CPT];
-        unpack<T>(__ldcs(reinterpret_cast<const typename V::type*>(
-                      N + (int64_t)(lo[0] + r) * ld + c0)),
-                  o);
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) v[j][r] = o[j];
-      }
-  } else {
-#pragma unroll
-    for (int j = 0; j < CPT; ++j)
-#pragma unroll
-      for (int r = 0; r < WM; ++r)
-        if (r < w[j]) v[j][r] = __ldcs(N + (int64_t)(lo[j] + r) * ld + c0 + j);
-  }
-
-  const bool force64 = allow_fb && (a.flags & ION_FORCE_FP64_COEF) != 0;
-  const bool no_fb = !allow_fb || (a.flags & ION_NO_FP64_FALLBACK) != 0;
-  const bool upd = (a.flags & ION_NO_WINDOW_UPDATE) == 0;
-  const T gap = (T)a.gap;
-  const T eps = (T)a.eps;
-  // One copy of the coefficient code serves the CPT cells: cell j's values
-  // are selected into registers, updated, and selected back.
-#pragma unroll 1
-  for (int j = 0; j < CPT; ++j) {
-    T vj[WM];
-    T Ej = Ev[0];
-    int loj = lo[0], hij = hi[0], wj = w[0];
-#pragma unroll
-    for (int r = 0; r < WM; ++r) vj[r] = v[0][r];
-#pragma unroll
-    for (int jj = 1; jj < CPT; ++jj)
-      if (j == jj) {
-        Ej = Ev[jj];
-        loj = lo[jj];
-        hij = hi[jj];
-        wj = w[jj];
-#pragma unroll
-        for (int r = 0; r < WM; ++r) vj[r] = v[jj][r];
-      }
-    bool fbj = false;
-    T dnej = T(0);
-    int nloj = loj, nhij = hij;
-    if (wj >= 2) {
-      const typename F::Field f = F::field(Ej);
-      T lam[WM];
-#pragma unroll
-      for (int r = 0; r < WM; ++r)
-        lam[r] = (r < wj - 1 && !a.zero_dt) ? F::rate(tab, loj + r, f) : T(0);
-      fbj = !no_fb &&
-            (force64 || (gap > T(0) && near_degenerate<T, WM>(lam, wj, gap)));
-      if (!fbj) {
-        dnej = window_update<T, WM>(vj, lam, wj);
-        if (upd) slide_window<T, WM>(vj, wj, a.Z, eps, nloj, nhij);
-      }
+    for (int r = 0; r < WM; ++r) {
+      lam[r] = (r < w - 1 && !a.zero_dt) ? F::rate(tab, lo + r, f) : T(0);
+      lmax = fmax(lmax, lam[r]);
     }
-#pragma unroll
-    for (int jj = 0; jj < CPT; ++jj)
-      if (j == jj) {
-        fb[jj] = fbj;
-        dne[jj] = dnej;
-        nlo[jj] = nloj;
-        nhi[jj] = nhij;
-#pragma unroll
-        for (int r = 0; r < WM; ++r) v[jj][r] = vj[r];
-      }
-  }
-
-  bool anyfb = false;
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) anyfb = anyfb || fb[j];
-  if (uni && !anyfb) {
-#pragma unroll
-    for (int r = 0; r < WM; ++r)
-      if (r < w[0]) {
-        T o[CPT];
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) o[j] = v[j][r];
-        __stcs(reinterpret_cast<typename V::type*>(N + (int64_t)(lo[0] + r) * ld + c0),
-               pack(o));
-      }
-  } else {
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      if (!ok[j] || fb[j]) continue;
-#pragma unroll
-      for (int r = 0; r < WM; ++r)
-        if (r < w[j]) __stcs(N + (int64_t)(lo[j] + r) * ld + c0 + j, v[j][r]);
-    }
-  }
-}
-
-// Loads the per-cell inputs of a thread, runs the warp's width bucket, and
-// stores dne and the windows.  Shared by the FP32 and FP64 kernels.
-template <class F, int CPT>
-__device__ __forceinline__ void step_thread(const StepArgs& a,
-                                            const typename F::Staged& tab,
-                                            bool allow_fb) {
-  using T = typename F::T;
-  using V = Vec16<T>;
-  const int64_t c0l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * CPT;
-  const int c0 = (int)(c0l < a.ncells ? c0l : a.ncells);
-  const bool full = c0l + CPT <= a.ncells;
-  const T* __restrict__ E = static_cast<const T*>(a.E);
-
-  T Ev[CPT];
-  int lo[CPT], hi[CPT];
-  bool ok[CPT];
-  if (full) {
-    unpack<T>(__ldcs(reinterpret_cast<const typename V::type*>(E + c0)), Ev);
-    if constexpr (CPT == 4) {
-      const uint32_t l4 = __ldcs(reinterpret_cast<const unsigned int*>(a.lo + c0));
-      const uint32_t h4 = __ldcs(reinterpret_cast<const unsigned int*>(a.hi + c0));
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        lo[j] = (l4 >> (8 * j)) & 0xff;
-        hi[j] = (h4 >> (8 * j)) & 0xff;
-      }
+    if (lmax <= DDParams<T>::prop_max) {
+      dne = taylor_propagate<T, WM>(v, lam, w, lmax);
     } else {
-      const uint32_t l2 = __ldcs(reinterpret_cast<const unsigned short*>(a.lo + c0));
-      const uint32_t h2 = __ldcs(reinterpret_cast<const unsigned short*>(a.hi + c0));
-#pragma unroll
-      for (int j = 0; j < CPT; ++j) {
-        lo[j] = (l2 >> (8 * j)) & 0xff;
-        hi[j] = (h2 >> (8 * j)) & 0xff;
-      }
+      if (allow_fb && (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
+          ((a.flags & ION_FORCE_FP64_COEF) != 0 ||
+           (a.gap > 0.0 && near_degenerate<T, WM>(lam, w, (T)a.gap))))
+        return true;
+      dne = dd_update<T, WM>(v, lam, w);
     }
-  } else {
+    if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
+      slide_window<T, WM>(v, w, a.Z, (T)a.eps, nlo, nhi);
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      const bool in = c0l + j < a.ncells;
-      Ev[j] = in ? E[c0 + j] : T(0);
-      lo[j] = in ? a.lo[c0 + j] : 1;
-      hi[j] = in ? a.hi[c0 + j] : 0;  // lo > hi: marks "no cell"
-    }
+    for (int r = 0; r < WM; ++r)
+      if (r < w) __stcs(N + (int64_t)(lo + r) * ld + c, v[r]);
+   }
   }
-  int wmax = 0, nbad = 0;
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    const bool in = c0l + j < a.ncells;
-    ok[j] = in && window_ok(lo[j], hi[j], a.Z);
-    nbad += (in && !ok[j]) ? 1 : 0;
-    wmax = ok[j] ? max(wmax, hi[j] - lo[j] + 1) : wmax;
-  }
-  if (nbad) atomicAdd(&a.hdr[kHdrInvalid], (unsigned)nbad);
-  const int WMw = __reduce_max_sync(kFull, wmax);
-
-  int nlo[CPT], nhi[CPT];
-  bool fb[CPT];
-  T dne[CPT];
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    nlo[j] = lo[j];
-    nhi[j] = hi[j];
-    fb[j] = false;
-    dne[j] = T(0);
-  }
-  switch (WMw) {
-    case 0:
-    case 1:
-      break;  // nothing moves; dne = 0
-    case 2:
-      cells<F, 2, CPT>(a, tab, c0, full, Ev, lo, hi, ok, nlo, nhi, fb, dne, allow_fb);
-      break;
-    case 3:
-      cells<F, 3, CPT>(a, tab, c0, full, Ev, lo, hi, ok, nlo, nhi, fb, dne, allow_fb);
-      break;
-    case 4:
-      cells<F, 4, CPT>(a, tab, c0, full, Ev, lo, hi, ok, nlo, nhi, fb, dne, allow_fb);
-      break;
-    case 5:
-      cells<F, 5, CPT>(a, tab, c0, full, Ev, lo, hi, ok, nlo, nhi, fb, dne, allow_fb);
-      break;
-    default:
-      cells<F, 6, CPT>(a, tab, c0, full, Ev, lo, hi, ok, nlo, nhi, fb, dne, allow_fb);
-      break;
-  }
-
-  // dne (x n_gas) and the windows of the cells this kernel finished
-  bool all = full;
-#pragma unroll
-  for (int j = 0; j < CPT; ++j) all = all && ok[j] && !fb[j];
-  T* __restrict__ D = static_cast<T*>(a.dne);
   const T* __restrict__ G = static_cast<const T*>(a.n_gas);
-  if (all) {
-    if (G) {
-      T g[CPT];
-      unpack<T>(__ldcs(reinterpret_cast<const typename V::type*>(G + c0)), g);
-#pragma unroll
-      for (int j = 0; j < CPT; ++j) dne[j] *= g[j];
-    }
-    __stcs(reinterpret_cast<typename V::type*>(D + c0), pack(dne));
-    uint32_t l = 0, h = 0;
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      l |= (uint32_t)nlo[j] << (8 * j);
-      h |= (uint32_t)nhi[j] << (8 * j);
-    }
-    if constexpr (CPT == 4) {
-      __stcs(reinterpret_cast<unsigned int*>(a.lo + c0), l);
-      __stcs(reinterpret_cast<unsigned int*>(a.hi + c0), h);
-    } else {
-      __stcs(reinterpret_cast<unsigned short*>(a.lo + c0), (unsigned short)l);
-      __stcs(reinterpret_cast<unsigned short*>(a.hi + c0), (unsigned short)h);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      if (!ok[j] || fb[j]) continue;
-      D[c0 + j] = G ? dne[j] * G[c0 + j] : dne[j];
-      a.lo[c0 + j] = (uint8_t)nlo[j];
-      a.hi[c0 + j] = (uint8_t)nhi[j];
-    }
+  __stcs(static_cast<T*>(a.dne) + c, G ? dne * G[c] : dne);
+  if (nlo != lo) {
+    a.lo[c] = (uint8_t)nlo;
+    a.hi[c] = (uint8_t)nhi;
   }
-  if (allow_fb) queue_append<CPT>(a, fb, c0);
+  return false;
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+// Dispatch on the warp's widest window (WMIN..WMAX instantiated).
+template <class F, int WMIN, int WMAX>
+__device__ __forceinline__ bool cell_bucket(int WMw, const StepArgs& a,
+                                            const typename F::Staged& tab,
+                                            int c, typename F::T Ec, int lo,
+                                            int hi, bool ok, bool allow_fb) {
+  if (!ok) return false;
+  if (WMIN <= 1 && WMw <= 1) return cell<F, 1>(a, tab, c, Ec, lo, hi, allow_fb);
+  if (WMIN <= 2 && WMAX >= 2 && WMw == 2) return cell<F, 2>(a, tab, c, Ec, lo, hi, allow_fb);
+  if (WMIN <= 3 && WMAX >= 3 && WMw == 3) return cell<F, 3>(a, tab, c, Ec, lo, hi, allow_fb);
+  if (WMIN <= 4 && WMAX >= 4 && WMw == 4) return cell<F, 4>(a, tab, c, Ec, lo, hi, allow_fb);
+  if (WMIN <= 5 && WMAX >= 5 && WMw == 5) return cell<F, 5>(a, tab, c, Ec, lo, hi, allow_fb);
+  if (WMAX >= 6 && WMw >= 6) return cell<F, 6>(a, tab, c, Ec, lo, hi, allow_fb);
+  return false;
+}
+
+// Loads this thread's cell; returns the widest valid window of the warp.
+template <class F>
+__device__ __forceinline__ int load_cell(const StepArgs& a, int c, bool in,
+                                         typename F::T& Ec, int& lo, int& hi,
+                                         bool& ok) {
+  using T = typename F::T;
+  Ec = in ? __ldcs(static_cast<const T*>(a.E) + c) : T(0);
+  lo = in ? __ldcs(a.lo + c) : 1;
+  hi = in ? __ldcs(a.hi + c) : 0;
+  ok = in && window_ok(lo, hi, a.Z);
+  return __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
+}
+
+__global__ void __launch_bounds__(kThreads)
     ion_step_f32_kernel(const __grid_constant__ StepArgs a) {
   __shared__ StagedF32 tab;
   stage_f32(a.tab, a.log2dt, &tab);
   __syncthreads();
-  step_thread<F32Form, 4>(a, tab, true);
+  const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = cl < a.ncells;
+  const int c = in ? (int)cl : 0;
+  float Ec;
+  int lo, hi;
+  bool ok;
+  const int WMw = load_cell<F32Form>(a, c, in, Ec, lo, hi, ok);
+  if (in && !ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
+  if (WMw > 4) {
+    // the warp's 32-cell chunk goes to the wide kernel
+    if ((threadIdx.x & 31) == 0)
+      a.wide[atomicAdd(&a.hdr[kHdrWide], 1u)] = (uint32_t)cl;
+    return;
+  }
+  const bool fb = cell_bucket<F32Form, 1, 4>(WMw, a, tab, c, Ec, lo, hi, ok, true);
+  warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
+}
+
+// The queued 32-cell chunks whose widest window has 5 or 6 states; one warp
+// per chunk.
+__global__ void __launch_bounds__(kThreads)
+    ion_step_f32_wide_kernel(const __grid_constant__ StepArgs a) {
+  __shared__ StagedF32 tab;
+  stage_f32(a.tab, a.log2dt, &tab);
+  __syncthreads();
+  const unsigned nchunks = *((volatile unsigned*)&a.hdr[kHdrWide]);
+  const int lane = threadIdx.x & 31;
+  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned i = warp; i < nchunks; i += nwarps) {
+    const int64_t cl = (int64_t)a.wide[i] + lane;
+    const bool in = cl < a.ncells;
+    const int c = in ? (int)cl : 0;
+    float Ec;
+    int lo, hi;
+    bool ok;
+    const int WMw = load_cell<F32Form>(a, c, in, Ec, lo, hi, ok);
+    const bool fb = cell_bucket<F32Form, 5, 6>(WMw, a, tab, c, Ec, lo, hi, ok, true);
+    warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -377,7 +203,15 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ StagedF64 tab;
   stage_f64(a.tab, a.log2dt, &tab);
   __syncthreads();
-  step_thread<F64Form, 2>(a, tab, false);
+  const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = cl < a.ncells;
+  const int c = in ? (int)cl : 0;
+  double Ec;
+  int lo, hi;
+  bool ok;
+  const int WMw = load_cell<F64Form>(a, c, in, Ec, lo, hi, ok);
+  if (in && !ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
+  cell_bucket<F64Form, 1, 6>(WMw, a, tab, c, Ec, lo, hi, ok, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -394,7 +228,7 @@ __device__ __forceinline__ void fb_cell(const StepArgs& a, const StagedF32& tab,
     v[r] = (double)N[(int64_t)(lo + r) * a.ld + c];
     lam[r] = (r < W - 1 && !a.zero_dt) ? (double)rate_dt_f32(tab, lo + r, f) : 0.0;
   }
-  const double dne = window_update<double, W>(v, lam, W);
+  const double dne = dd_update<double, W>(v, lam, W);
   float vf[W];
 #pragma unroll
   for (int r = 0; r < W; ++r) {
@@ -445,15 +279,30 @@ __global__ void __launch_bounds__(128)
 
 }  // namespace
 
+size_t step_workspace_bytes(int64_t ncells, bool f64) {
+  if (f64) return kHdrBytes;
+  const size_t q = 4 * (size_t)ncells;
+  const size_t wide = 4 * (size_t)((ncells + 31) / 32);
+  return kHdrBytes + (q + 255) / 256 * 256 + wide;
+}
+
+void bind_workspace(StepArgs& a, void* ws) {
+  char* p = static_cast<char*>(ws);
+  a.hdr = reinterpret_cast<uint32_t*>(p);
+  a.queue = reinterpret_cast<uint32_t*>(p + kHdrBytes);
+  const size_t q = 4 * (size_t)a.ncells;
+  a.wide = reinterpret_cast<uint32_t*>(p + kHdrBytes + (q + 255) / 256 * 256);
+}
+
 cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(a.hdr, 0, 2 * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(a.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   if (a.ncells == 0) return cudaSuccess;
-  const int64_t per_block = (int64_t)kThreads * 4;
-  const int blocks = (int)((a.ncells + per_block - 1) / per_block);
+  const int blocks = (int)((a.ncells + kThreads - 1) / kThreads);
   ion_step_f32_kernel<<<blocks, kThreads, 0, s>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ion_step_f32_wide_kernel<<<4 * num_sms, kThreads, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const bool need_fb = (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
                        ((a.flags & ION_FORCE_FP64_COEF) != 0 || a.gap > 0.0);
   if (need_fb) {
@@ -464,11 +313,10 @@ cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
 }
 
 cudaError_t launch_step_f64(const StepArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(a.hdr, 0, 2 * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(a.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   if (a.ncells == 0) return cudaSuccess;
-  const int64_t per_block = (int64_t)kThreads * 2;
-  const int blocks = (int)((a.ncells + per_block - 1) / per_block);
+  const int blocks = (int)((a.ncells + kThreads - 1) / kThreads);
   ion_step_f64_kernel<<<blocks, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }

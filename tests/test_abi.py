@@ -60,5 +60,8 @@ def test_host_side_rejections():
 
 def test_workspace_sizes():
     assert ionize.workspace_bytes(0) == 256
-    assert ionize.workspace_bytes(1000) == 256 + 4000
+    # header + one queue slot per cell + one slot per 32-cell chunk
+    for n in (1, 31, 32, 1000, 33554432):
+        assert ionize.workspace_bytes(n) >= 256 + 4 * n + 4 * ((n + 31) // 32)
+        assert ionize.workspace_bytes(n) <= 512 + 4 * n + 4 * ((n + 31) // 32)
     assert ionize.workspace_bytes(1000, ionize.ION_F64_PLAIN) == 256
