@@ -102,6 +102,14 @@ __device__ __forceinline__ FieldF32 field_f32(float E_in) {
   return f;
 }
 
+// 2^x by the SFU (ex2.approx.ftz.f32: about 2 ulp; results below 2^-126
+// flush to 0, which no population can see).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
@@ -122,7 +130,7 @@ __device__ __forceinline__ float rate_dt_f32(const StagedF32& t, int k,
   const float bh = t.b_hi[k];
   if (!Precise) {
     const float y0 = fmaf(-bh, f.lg, t.a_hi[k]) - q;
-    if (y0 < -12.0f) return exp2f(y0);
+    if (y0 < -12.0f) return ex2_approx(y0);
   }
   const float ql = (fmaf(-q, f.E, Ch) + t.C_lo[k]) * f.rE;  // C/E = q + ql
   const float p = bh * f.ex;
@@ -141,7 +149,7 @@ __device__ __forceinline__ float rate_dt_f32(const StagedF32& t, int k,
   }
   float y = s2 + tail;
   y = fminf(y, 99.0f);  // W dt <= 2^99: keeps every later product finite
-  return exp2f(y);
+  return ex2_approx(y);
 }
 
 __device__ __forceinline__ double rate_dt_f64(const StagedF64& t, int k,
@@ -332,11 +340,11 @@ __device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
 // below (2 prop_max)^(R+1)/(R+1)!.  inc[] collects N' - N without forming
 // the difference, so the freed electrons carry no cancellation.
 //   v, lam, w as in dd_update below; returns the electrons released.
-template <typename T, int WM>
+template <typename T, int WM, int PMAX = DDParams<T>::PMAX>
 __device__ __forceinline__ T taylor_propagate(T (&v)[WM], const T (&lam)[WM],
                                               int w, T lmax) {
   using P = DDParams<T>;
-  const int R = P::terms(T(2) * lmax, P::PMAX);
+  const int R = P::terms(T(2) * lmax, PMAX);
   T t[WM], inc[WM];
 #pragma unroll
   for (int i = 0; i < WM; ++i) {
@@ -344,7 +352,7 @@ __device__ __forceinline__ T taylor_propagate(T (&v)[WM], const T (&lam)[WM],
     inc[i] = T(0);
   }
 #pragma unroll
-  for (int k = 1; k <= P::PMAX; ++k) {
+  for (int k = 1; k <= PMAX; ++k) {
     if (k > R) break;
     const T rk = T(1.0 / k);
 #pragma unroll

@@ -1,18 +1,24 @@
 // step.cu -- the ion_step kernels.
 //
 // FP32 form (ION_F32), three kernels on the caller's stream:
-//   ion_step_f32_kernel   one cell per thread over all cells.  A warp whose
-//                         32 cells all have windows of <= 4 states finishes
-//                         them here; a warp holding a wider window is queued
-//                         whole (one entry per 32-cell chunk) so that the
-//                         wide code paths do not set this kernel's register
-//                         budget.  Cells with a nearly degenerate rate pair
-//                         are left untouched and queued one by one.
-//   ion_step_f32_wide_kernel   the queued 32-cell chunks (windows of 5-6).
-//   ion_step_fb_kernel    the queued cells: the same FP32 rates, FP64
-//                         Bateman coefficients and propagation, rounded back.
+//   ion_step_f32_kernel       persistent, one cell per thread per pass over
+//                             all cells and every window width.  It finishes
+//                             the cells whose rates all have W dt <= 0.025
+//                             (at most four Taylor terms of exp(dt A)); the
+//                             others ("hard" cells) are left untouched and
+//                             queued, so that warps doing the long work are
+//                             made of hard cells only.  In a laser field the
+//                             instantaneous |E| swings from zero to its peak
+//                             every few cells, so without this split almost
+//                             every warp near the pulse would run the longest
+//                             path of its lanes.
+//   ion_step_f32_hard_kernel  the queued cells: Taylor form up to W dt <= 1,
+//                             divided-difference (Bateman) form above; cells
+//                             with a nearly degenerate rate pair go on to
+//   ion_step_fb_kernel        FP32 rates, FP64 Bateman coefficients and
+//                             propagation, rounded back.
 // Plain FP64 form (ION_F64_PLAIN): ion_step_f64_kernel, one cell per thread,
-// every width inline.
+// every width and path inline.
 //
 // One step is Eqs. 1-9 of the paper per cell; see ion_device.cuh.
 #include <cstdint>
@@ -151,49 +157,129 @@ __device__ __forceinline__ int load_cell(const StepArgs& a, int c, bool in,
   return __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
 }
 
+// Kernel A's cell: finishes it if every W dt <= kLamEasy, else returns true
+// (the cell is left untouched for the hard kernel).
+constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms suffice
+constexpr int kEasyTerms = 4;
+
+template <int WM>
+__device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& tab,
+                                          int c, float Ec, int lo, int hi) {
+  float* __restrict__ N = static_cast<float*>(a.N);
+  const int64_t ld = a.ld;
+  const int w = hi - lo + 1;
+  float v[WM];
+#pragma unroll
+  for (int r = 0; r < WM; ++r)
+    v[r] = r < w ? __ldcs(N + (int64_t)(lo + r) * ld + c) : 0.0f;
+  float dne = 0.0f;
+  int nlo = lo, nhi = hi;
+  if constexpr (WM >= 2) {
+    if (w >= 2) {
+      const FieldF32 f = field_f32(Ec);
+      float lam[WM];
+      float lmax = 0.0f;
+#pragma unroll
+      for (int r = 0; r < WM; ++r) {
+        lam[r] = (r < w - 1 && !a.zero_dt) ? rate_dt_f32(tab, lo + r, f) : 0.0f;
+        lmax = fmaxf(lmax, lam[r]);
+      }
+      if (lmax > kLamEasy) return true;
+      dne = taylor_propagate<float, WM, kEasyTerms>(v, lam, w, lmax);
+      if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
+        slide_window<float, WM>(v, w, a.Z, (float)a.eps, nlo, nhi);
+#pragma unroll
+      for (int r = 0; r < WM; ++r)
+        if (r < w) __stcs(N + (int64_t)(lo + r) * ld + c, v[r]);
+    }
+  }
+  const float* __restrict__ G = static_cast<const float*>(a.n_gas);
+  __stcs(static_cast<float*>(a.dne) + c, G ? dne * G[c] : dne);
+  if (nlo != lo) {
+    a.lo[c] = (uint8_t)nlo;
+    a.hi[c] = (uint8_t)nhi;
+  }
+  return false;
+}
+
 __global__ void __launch_bounds__(kThreads)
     ion_step_f32_kernel(const __grid_constant__ StepArgs a) {
   __shared__ StagedF32 tab;
   stage_f32(a.tab, a.log2dt, &tab);
   __syncthreads();
-  const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = cl < a.ncells;
-  const int c = in ? (int)cl : 0;
-  float Ec;
-  int lo, hi;
-  bool ok;
-  const int WMw = load_cell<F32Form>(a, c, in, Ec, lo, hi, ok);
-  if (in && !ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
-  if (WMw > 4) {
-    // the warp's 32-cell chunk goes to the wide kernel
-    if ((threadIdx.x & 31) == 0)
-      a.wide[atomicAdd(&a.hdr[kHdrWide], 1u)] = (uint32_t)cl;
-    return;
-  }
-  const bool fb = cell_bucket<F32Form, 1, 4>(WMw, a, tab, c, Ec, lo, hi, ok, true);
-  warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
-}
-
-// The queued 32-cell chunks whose widest window has 5 or 6 states; one warp
-// per chunk.
-__global__ void __launch_bounds__(kThreads)
-    ion_step_f32_wide_kernel(const __grid_constant__ StepArgs a) {
-  __shared__ StagedF32 tab;
-  stage_f32(a.tab, a.log2dt, &tab);
-  __syncthreads();
-  const unsigned nchunks = *((volatile unsigned*)&a.hdr[kHdrWide]);
-  const int lane = threadIdx.x & 31;
-  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (unsigned i = warp; i < nchunks; i += nwarps) {
-    const int64_t cl = (int64_t)a.wide[i] + lane;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+       cl - threadIdx.x < a.ncells; cl += stride) {
     const bool in = cl < a.ncells;
     const int c = in ? (int)cl : 0;
     float Ec;
     int lo, hi;
     bool ok;
     const int WMw = load_cell<F32Form>(a, c, in, Ec, lo, hi, ok);
-    const bool fb = cell_bucket<F32Form, 5, 6>(WMw, a, tab, c, Ec, lo, hi, ok, true);
+    if (in && !ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
+    bool hard = false;
+    if (ok) {
+      switch (WMw) {
+        case 1:
+          hard = easy_cell<1>(a, tab, c, Ec, lo, hi);
+          break;
+        case 2:
+          hard = easy_cell<2>(a, tab, c, Ec, lo, hi);
+          break;
+        case 3:
+          hard = easy_cell<3>(a, tab, c, Ec, lo, hi);
+          break;
+        case 4:
+          hard = easy_cell<4>(a, tab, c, Ec, lo, hi);
+          break;
+        case 5:
+          hard = easy_cell<5>(a, tab, c, Ec, lo, hi);
+          break;
+        default:
+          hard = easy_cell<6>(a, tab, c, Ec, lo, hi);
+          break;
+      }
+    }
+    warp_append(&a.hdr[kHdrHard], a.hard, hard, (uint32_t)c);
+  }
+}
+
+// The hard cells, one per thread, each with its own width.
+__global__ void __launch_bounds__(kThreads)
+    ion_step_f32_hard_kernel(const __grid_constant__ StepArgs a) {
+  __shared__ StagedF32 tab;
+  stage_f32(a.tab, a.log2dt, &tab);
+  __syncthreads();
+  const unsigned n = *((volatile unsigned*)&a.hdr[kHdrHard]);
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
+    const bool in = i < n;
+    const int c = in ? (int)a.hard[i] : 0;
+    const int lo = in ? a.lo[c] : 0, hi = in ? a.hi[c] : 0;
+    const float Ec = in ? static_cast<const float*>(a.E)[c] : 0.0f;
+    bool fb = false;
+    if (in) {
+      switch (hi - lo + 1) {
+        case 2:
+          fb = cell<F32Form, 2>(a, tab, c, Ec, lo, hi, true);
+          break;
+        case 3:
+          fb = cell<F32Form, 3>(a, tab, c, Ec, lo, hi, true);
+          break;
+        case 4:
+          fb = cell<F32Form, 4>(a, tab, c, Ec, lo, hi, true);
+          break;
+        case 5:
+          fb = cell<F32Form, 5>(a, tab, c, Ec, lo, hi, true);
+          break;
+        case 6:
+          fb = cell<F32Form, 6>(a, tab, c, Ec, lo, hi, true);
+          break;
+        default:
+          break;
+      }
+    }
     warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
   }
 }
@@ -281,27 +367,43 @@ __global__ void __launch_bounds__(128)
 
 size_t step_workspace_bytes(int64_t ncells, bool f64) {
   if (f64) return kHdrBytes;
-  const size_t q = 4 * (size_t)ncells;
-  const size_t wide = 4 * (size_t)((ncells + 31) / 32);
-  return kHdrBytes + (q + 255) / 256 * 256 + wide;
+  const size_t q = (4 * (size_t)ncells + 255) / 256 * 256;
+  return kHdrBytes + 2 * q;
 }
 
 void bind_workspace(StepArgs& a, void* ws) {
   char* p = static_cast<char*>(ws);
   a.hdr = reinterpret_cast<uint32_t*>(p);
+  const size_t q = (4 * (size_t)a.ncells + 255) / 256 * 256;
   a.queue = reinterpret_cast<uint32_t*>(p + kHdrBytes);
-  const size_t q = 4 * (size_t)a.ncells;
-  a.wide = reinterpret_cast<uint32_t*>(p + kHdrBytes + (q + 255) / 256 * 256);
+  a.hard = reinterpret_cast<uint32_t*>(p + kHdrBytes + q);
 }
+
+namespace {
+int resident_blocks_f32() {
+  static int blocks = 0;
+  if (!blocks) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ion_step_f32_kernel, kThreads, 0) !=
+            cudaSuccess ||
+        b < 1)
+      b = 1;
+    blocks = b;
+  }
+  return blocks;
+}
+}  // namespace
 
 cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   if (a.ncells == 0) return cudaSuccess;
-  const int blocks = (int)((a.ncells + kThreads - 1) / kThreads);
+  const int64_t tiles = (a.ncells + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)resident_blocks_f32() * num_sms;
+  const int blocks = (int)(tiles < cap ? tiles : cap);
   ion_step_f32_kernel<<<blocks, kThreads, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ion_step_f32_wide_kernel<<<4 * num_sms, kThreads, 0, s>>>(a);
+  ion_step_f32_hard_kernel<<<4 * num_sms, kThreads, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const bool need_fb = (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
                        ((a.flags & ION_FORCE_FP64_COEF) != 0 || a.gap > 0.0);

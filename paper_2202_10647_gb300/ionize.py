@@ -232,3 +232,9 @@ def counters(ws: torch.Tensor):
     of the last step that used `ws` (synchronizes)."""
     h = ws[:8].cpu().view(torch.int32)
     return int(h[0]), int(h[1])
+
+
+def stiff_cells(ws: torch.Tensor) -> int:
+    """Cells the last FP32 step that used `ws` finished in its second kernel
+    (some W dt > 0.025); synchronizes."""
+    return int(ws[8:12].cpu().view(torch.int32)[0])

@@ -60,8 +60,7 @@ def test_host_side_rejections():
 
 def test_workspace_sizes():
     assert ionize.workspace_bytes(0) == 256
-    # header + one queue slot per cell + one slot per 32-cell chunk
+    # header + two queues of one slot per cell
     for n in (1, 31, 32, 1000, 33554432):
-        assert ionize.workspace_bytes(n) >= 256 + 4 * n + 4 * ((n + 31) // 32)
-        assert ionize.workspace_bytes(n) <= 512 + 4 * n + 4 * ((n + 31) // 32)
+        assert 256 + 8 * n <= ionize.workspace_bytes(n) <= 768 + 8 * n
     assert ionize.workspace_bytes(1000, ionize.ION_F64_PLAIN) == 256
