@@ -119,9 +119,8 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
               int k_hi, void* W_out, int64_t ldw, int dtype, void* stream);
 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
- * a 256-byte header plus, for ION_F32, two queues of one 4-byte slot per cell
- * (cells finished by a second kernel because a rate has W dt > 0.025, and
- * cells whose coefficients are computed in FP64). */
+ * a 256-byte header plus, for ION_F32, a queue of one 4-byte slot per cell
+ * (cells whose Bateman coefficients are computed in FP64). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
 
 /* ion_step -- advance the charge-state populations of every cell by one
@@ -159,9 +158,10 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *          the step the header holds uint32 counters: word 0 the cells
  *          whose coefficients were computed in FP64, word 1 the cells left
  *          untouched because their window was invalid (lo > hi, hi > Z or
- *          w > ION_MAX_WINDOW), word 2 the cells finished by the second
- *          (stiff-cell) kernel.
- * Alignment: E, N, dne, n_gas aligned to their element size.
+ *          w > ION_MAX_WINDOW), word 2 the cells that had a rate with
+ *          W dt > 0.025 (finished on the long path).
+ * Alignment: E, N, dne, n_gas aligned to their element size; with ION_F32
+ * k_lo and k_hi 4-byte aligned (they are copied four cells at a time).
  * Calls that share a workspace must not overlap on the device.
  * Errors: ION_EINVAL (checked before any launch), ION_ECUDA. */
 ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,

@@ -246,6 +246,8 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
     if (!aligned(E, el) || !aligned(N, el) || !aligned(dne, el) ||
         (n_gas && !aligned(n_gas, el)))
       return fail(ION_EINVAL, "E, N, dne and n_gas must be aligned to their element size");
+    if (!f64 && (!aligned(k_lo, 4) || !aligned(k_hi, 4)))
+      return fail(ION_EINVAL, "k_lo and k_hi must be 4-byte aligned");
   }
   ion::StepArgs a;
   a.tab = sp->dev;

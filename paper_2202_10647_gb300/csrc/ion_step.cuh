@@ -12,7 +12,7 @@ namespace ion {
 // Workspace header (uint32 words at the start of the workspace).
 constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
 constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
-constexpr int kHdrHard = 2;      // cells queued for the hard-cell kernel
+constexpr int kHdrStiff = 2;     // cells finished through the per-warp stiff lists
 constexpr int kHdrWords = 3;
 constexpr size_t kHdrBytes = 256;
 
@@ -34,7 +34,6 @@ struct StepArgs {
   int flags;
   uint32_t* hdr;    // workspace header (kHdr* words)
   uint32_t* queue;  // cells for the FP64-coefficient kernel
-  uint32_t* hard;   // cells for the hard-cell kernel
 };
 
 // Workspace layout (step.cu).

@@ -1,22 +1,21 @@
 // step.cu -- the ion_step kernels.
 //
-// FP32 form (ION_F32), three kernels on the caller's stream:
-//   ion_step_f32_kernel       persistent, one cell per thread per pass over
-//                             all cells and every window width.  It finishes
-//                             the cells whose rates all have W dt <= 0.025
-//                             (at most four Taylor terms of exp(dt A)); the
-//                             others ("hard" cells) are left untouched and
-//                             queued, so that warps doing the long work are
-//                             made of hard cells only.  In a laser field the
-//                             instantaneous |E| swings from zero to its peak
-//                             every few cells, so without this split almost
-//                             every warp near the pulse would run the longest
-//                             path of its lanes.
-//   ion_step_f32_hard_kernel  the queued cells: Taylor form up to W dt <= 1,
-//                             divided-difference (Bateman) form above; cells
-//                             with a nearly degenerate rate pair go on to
-//   ion_step_fb_kernel        FP32 rates, FP64 Bateman coefficients and
-//                             propagation, rounded back.
+// FP32 form (ION_F32), two kernels on the caller's stream:
+//   ion_step_f32_kernel  persistent; every warp walks its own sequence of
+//       32-cell chunks through a 4-stage ring in shared memory.  cp.async
+//       brings |E|, k_lo and k_hi in two chunks ahead and each lane's own
+//       window planes one chunk ahead, so the loads in flight do not cost
+//       registers and the traffic is exactly the cells' windows.  A cell
+//       whose rates all have W dt <= 0.025 is finished at once (at most four
+//       Taylor terms of exp(dt A)); the others ("stiff" cells) are copied with
+//       their inputs into a per-warp list in shared memory and finished 32 at
+//       a time, so the long paths run in full warps.  (In a laser field |E|
+//       swings from zero to its peak every few cells, so most warps near the
+//       pulse hold a few stiff cells.)  Stiff cells take the Taylor form up to
+//       W dt <= 1 and the divided-difference (Bateman) form above; cells with
+//       a nearly degenerate rate pair are left untouched and queued for
+//   ion_step_fb_kernel   FP32 rates, FP64 Bateman coefficients and
+//       propagation, rounded back to FP32.
 // Plain FP64 form (ION_F64_PLAIN): ion_step_f64_kernel, one cell per thread,
 // every width and path inline.
 //
@@ -31,10 +30,32 @@ namespace ion {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;       // FP64 kernel
+constexpr int kWarps = 4;           // warps per block of the FP32 kernel
+constexpr int kStages = 4;          // chunks in the per-warp ring
+constexpr int kStiffCap = 64;       // per-warp list of stiff cells
+constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms
+constexpr int kEasyTerms = 4;
 
 __device__ __forceinline__ bool window_ok(int lo, int hi, int Z) {
   return lo <= hi && hi <= Z && hi - lo + 1 <= ION_MAX_WINDOW;
+}
+
+// ---------------------------------------------------------------------------
+// cp.async (global -> shared, 4 bytes, completion tracked per thread in
+// commit groups; no spin loop is involved).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // Per-precision hooks of the generic cell code.
@@ -74,50 +95,47 @@ __device__ __forceinline__ void warp_append(uint32_t* counter, uint32_t* queue,
 }
 
 // ---------------------------------------------------------------------------
-// One cell (index c, window [lo, hi] of width w <= WM, validated).
-// Returns true if the cell was left to the FP64 queue.
+// Full update of one cell whose window populations v[0..w-1] are loaded
+// (w <= WM): rates, Taylor or Bateman form, window slide, stores.  Returns
+// true (and stores nothing) if the cell goes to the FP64 queue.
 // ---------------------------------------------------------------------------
 template <class F, int WM>
-__device__ __forceinline__ bool cell(const StepArgs& a,
-                                     const typename F::Staged& tab, int c,
-                                     typename F::T Ec, int lo, int hi,
-                                     bool allow_fb) {
+__device__ __forceinline__ bool finish_cell(const StepArgs& a,
+                                            const typename F::Staged& tab, int c,
+                                            typename F::T Ec, int lo, int hi,
+                                            typename F::T (&v)[WM],
+                                            bool allow_fb) {
   using T = typename F::T;
   T* __restrict__ N = static_cast<T*>(a.N);
   const int64_t ld = a.ld;
   const int w = hi - lo + 1;
-  T v[WM];
-#pragma unroll
-  for (int r = 0; r < WM; ++r)
-    v[r] = r < w ? __ldcs(N + (int64_t)(lo + r) * ld + c) : T(0);
-
   T dne = T(0);
   int nlo = lo, nhi = hi;
   if constexpr (WM >= 2) {
-   if (w >= 2) {
-    const typename F::Field f = F::field(Ec);
-    T lam[WM];
-    T lmax = T(0);
+    if (w >= 2) {
+      const typename F::Field f = F::field(Ec);
+      T lam[WM];
+      T lmax = T(0);
 #pragma unroll
-    for (int r = 0; r < WM; ++r) {
-      lam[r] = (r < w - 1 && !a.zero_dt) ? F::rate(tab, lo + r, f) : T(0);
-      lmax = fmax(lmax, lam[r]);
-    }
-    if (lmax <= DDParams<T>::prop_max) {
-      dne = taylor_propagate<T, WM>(v, lam, w, lmax);
-    } else {
-      if (allow_fb && (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
-          ((a.flags & ION_FORCE_FP64_COEF) != 0 ||
-           (a.gap > 0.0 && near_degenerate<T, WM>(lam, w, (T)a.gap))))
-        return true;
-      dne = dd_update<T, WM>(v, lam, w);
-    }
-    if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
-      slide_window<T, WM>(v, w, a.Z, (T)a.eps, nlo, nhi);
+      for (int r = 0; r < WM; ++r) {
+        lam[r] = (r < w - 1 && !a.zero_dt) ? F::rate(tab, lo + r, f) : T(0);
+        lmax = fmax(lmax, lam[r]);
+      }
+      if (lmax <= DDParams<T>::prop_max) {
+        dne = taylor_propagate<T, WM>(v, lam, w, lmax);
+      } else {
+        if (allow_fb && (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
+            ((a.flags & ION_FORCE_FP64_COEF) != 0 ||
+             (a.gap > 0.0 && near_degenerate<T, WM>(lam, w, (T)a.gap))))
+          return true;
+        dne = dd_update<T, WM>(v, lam, w);
+      }
+      if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
+        slide_window<T, WM>(v, w, a.Z, (T)a.eps, nlo, nhi);
 #pragma unroll
-    for (int r = 0; r < WM; ++r)
-      if (r < w) __stcs(N + (int64_t)(lo + r) * ld + c, v[r]);
-   }
+      for (int r = 0; r < WM; ++r)
+        if (r < w) __stcs(N + (int64_t)(lo + r) * ld + c, v[r]);
+    }
   }
   const T* __restrict__ G = static_cast<const T*>(a.n_gas);
   __stcs(static_cast<T*>(a.dne) + c, G ? dne * G[c] : dne);
@@ -128,50 +146,78 @@ __device__ __forceinline__ bool cell(const StepArgs& a,
   return false;
 }
 
-// Dispatch on the warp's widest window (WMIN..WMAX instantiated).
-template <class F, int WMIN, int WMAX>
-__device__ __forceinline__ bool cell_bucket(int WMw, const StepArgs& a,
-                                            const typename F::Staged& tab,
-                                            int c, typename F::T Ec, int lo,
-                                            int hi, bool ok, bool allow_fb) {
-  if (!ok) return false;
-  if (WMIN <= 1 && WMw <= 1) return cell<F, 1>(a, tab, c, Ec, lo, hi, allow_fb);
-  if (WMIN <= 2 && WMAX >= 2 && WMw == 2) return cell<F, 2>(a, tab, c, Ec, lo, hi, allow_fb);
-  if (WMIN <= 3 && WMAX >= 3 && WMw == 3) return cell<F, 3>(a, tab, c, Ec, lo, hi, allow_fb);
-  if (WMIN <= 4 && WMAX >= 4 && WMw == 4) return cell<F, 4>(a, tab, c, Ec, lo, hi, allow_fb);
-  if (WMIN <= 5 && WMAX >= 5 && WMw == 5) return cell<F, 5>(a, tab, c, Ec, lo, hi, allow_fb);
-  if (WMAX >= 6 && WMw >= 6) return cell<F, 6>(a, tab, c, Ec, lo, hi, allow_fb);
-  return false;
-}
-
-// Loads this thread's cell; returns the widest valid window of the warp.
-template <class F>
-__device__ __forceinline__ int load_cell(const StepArgs& a, int c, bool in,
-                                         typename F::T& Ec, int& lo, int& hi,
-                                         bool& ok) {
+// The same, loading the window from global memory; W bounds the width.
+template <class F, int W>
+__device__ __forceinline__ bool global_cell(const StepArgs& a,
+                                            const typename F::Staged& tab, int c,
+                                            typename F::T Ec, int lo, int hi,
+                                            bool allow_fb) {
   using T = typename F::T;
-  Ec = in ? __ldcs(static_cast<const T*>(a.E) + c) : T(0);
-  lo = in ? __ldcs(a.lo + c) : 1;
-  hi = in ? __ldcs(a.hi + c) : 0;
-  ok = in && window_ok(lo, hi, a.Z);
-  return __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
+  const T* __restrict__ N = static_cast<const T*>(a.N);
+  T v[W];
+#pragma unroll
+  for (int r = 0; r < W; ++r)
+    v[r] = r < hi - lo + 1 ? __ldcs(N + (int64_t)(lo + r) * a.ld + c) : T(0);
+  return finish_cell<F, W>(a, tab, c, Ec, lo, hi, v, allow_fb);
 }
 
-// Kernel A's cell: finishes it if every W dt <= kLamEasy, else returns true
-// (the cell is left untouched for the hard kernel).
-constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms suffice
-constexpr int kEasyTerms = 4;
+// Dispatch on a width known to be 1..6 (per-lane switch).
+template <class F>
+__device__ __forceinline__ bool global_cell_any(const StepArgs& a,
+                                                const typename F::Staged& tab,
+                                                int c, typename F::T Ec, int lo,
+                                                int hi, bool allow_fb) {
+  switch (hi - lo + 1) {
+    case 1:
+      return global_cell<F, 1>(a, tab, c, Ec, lo, hi, allow_fb);
+    case 2:
+      return global_cell<F, 2>(a, tab, c, Ec, lo, hi, allow_fb);
+    case 3:
+      return global_cell<F, 3>(a, tab, c, Ec, lo, hi, allow_fb);
+    case 4:
+      return global_cell<F, 4>(a, tab, c, Ec, lo, hi, allow_fb);
+    case 5:
+      return global_cell<F, 5>(a, tab, c, Ec, lo, hi, allow_fb);
+    default:
+      return global_cell<F, 6>(a, tab, c, Ec, lo, hi, allow_fb);
+  }
+}
 
+// ---------------------------------------------------------------------------
+// FP32 streaming kernel: per-warp shared memory.
+// ---------------------------------------------------------------------------
+struct ChunkStage {
+  float E[32];
+  uint8_t lo[32];
+  uint8_t hi[32];
+  float P[ION_MAX_WINDOW][32];  // P[r][lane] = N[lo + r] of the lane's cell
+};
+
+struct StiffList {
+  float E[kStiffCap];
+  int c[kStiffCap];
+  uint8_t lo[kStiffCap];
+  uint8_t hi[kStiffCap];
+  float V[ION_MAX_WINDOW][kStiffCap];
+};
+
+struct WarpSmem {
+  ChunkStage st[kStages];
+  StiffList sl;
+};
+
+// Easy path of a lane's cell in a staged chunk: finishes it if every
+// W dt <= kLamEasy and returns false, else returns true untouched.
 template <int WM>
 __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& tab,
-                                          int c, float Ec, int lo, int hi) {
+                                          const ChunkStage& st, int lane, int c,
+                                          float Ec, int lo, int hi) {
   float* __restrict__ N = static_cast<float*>(a.N);
   const int64_t ld = a.ld;
   const int w = hi - lo + 1;
   float v[WM];
 #pragma unroll
-  for (int r = 0; r < WM; ++r)
-    v[r] = r < w ? __ldcs(N + (int64_t)(lo + r) * ld + c) : 0.0f;
+  for (int r = 0; r < WM; ++r) v[r] = r < w ? st.P[r][lane] : 0.0f;
   float dne = 0.0f;
   int nlo = lo, nhi = hi;
   if constexpr (WM >= 2) {
@@ -202,102 +248,197 @@ __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& ta
   return false;
 }
 
-__global__ void __launch_bounds__(kThreads)
+// Finishes `cnt` (<= 32) entries of the stiff list starting at `first`, one
+// per lane.  Every lane of the warp calls this.
+__device__ __forceinline__ void drain_stiff(const StepArgs& a, const StagedF32& tab,
+                                            const StiffList& sl, int first, int cnt,
+                                            int lane) {
+  bool fb = false;
+  int c = 0;
+  if (lane == 0) atomicAdd(&a.hdr[kHdrStiff], (unsigned)cnt);
+  if (lane < cnt) {
+    const int e = first + lane;
+    c = sl.c[e];
+    const int lo = sl.lo[e], hi = sl.hi[e];
+    const float Ec = sl.E[e];
+    switch (hi - lo + 1) {
+      case 2: {
+        float v[2] = {sl.V[0][e], sl.V[1][e]};
+        fb = finish_cell<F32Form, 2>(a, tab, c, Ec, lo, hi, v, true);
+      } break;
+      case 3: {
+        float v[3] = {sl.V[0][e], sl.V[1][e], sl.V[2][e]};
+        fb = finish_cell<F32Form, 3>(a, tab, c, Ec, lo, hi, v, true);
+      } break;
+      case 4: {
+        float v[4] = {sl.V[0][e], sl.V[1][e], sl.V[2][e], sl.V[3][e]};
+        fb = finish_cell<F32Form, 4>(a, tab, c, Ec, lo, hi, v, true);
+      } break;
+      case 5: {
+        float v[5] = {sl.V[0][e], sl.V[1][e], sl.V[2][e], sl.V[3][e], sl.V[4][e]};
+        fb = finish_cell<F32Form, 5>(a, tab, c, Ec, lo, hi, v, true);
+      } break;
+      default: {
+        float v[6] = {sl.V[0][e], sl.V[1][e], sl.V[2][e],
+                      sl.V[3][e], sl.V[4][e], sl.V[5][e]};
+        fb = finish_cell<F32Form, 6>(a, tab, c, Ec, lo, hi, v, true);
+      } break;
+    }
+  }
+  warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 4)
     ion_step_f32_kernel(const __grid_constant__ StepArgs a) {
   __shared__ StagedF32 tab;
+  __shared__ WarpSmem wsm[kWarps];
   stage_f32(a.tab, a.log2dt, &tab);
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-       cl - threadIdx.x < a.ncells; cl += stride) {
-    const bool in = cl < a.ncells;
-    const int c = in ? (int)cl : 0;
-    float Ec;
-    int lo, hi;
-    bool ok;
-    const int WMw = load_cell<F32Form>(a, c, in, Ec, lo, hi, ok);
-    if (in && !ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
-    bool hard = false;
+
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  WarpSmem& S = wsm[wib];
+  const int gw = blockIdx.x * kWarps + wib;
+  const int TW = gridDim.x * kWarps;
+  const int nfull = a.ncells >> 5;
+  const int K = gw < nfull ? (nfull - 1 - gw) / TW + 1 : 0;
+  const float* __restrict__ E = static_cast<const float*>(a.E);
+  const float* __restrict__ N = static_cast<const float*>(a.N);
+  const int64_t ld = a.ld;
+
+  // |E|, k_lo, k_hi of the warp's chunk k into its stage (one commit group).
+  auto issue_front = [&](int k) {
+    if (k < K) {
+      const int c0 = (gw + k * TW) << 5;
+      ChunkStage& st = S.st[k % kStages];
+      cp_async4(&st.E[lane], E + c0 + lane);
+      if (lane < 8)
+        cp_async4(&st.lo[4 * lane], a.lo + c0 + 4 * lane);
+      else if (lane < 16)
+        cp_async4(&st.hi[4 * (lane - 8)], a.hi + c0 + 4 * (lane - 8));
+    }
+    cp_async_commit();
+  };
+  // the window planes of the lane's cell of chunk k (one commit group).
+  auto issue_planes = [&](int k) {
+    if (k < K) {
+      const int c = ((gw + k * TW) << 5) + lane;
+      ChunkStage& st = S.st[k % kStages];
+      const int lo = st.lo[lane], hi = st.hi[lane];
+      const int w = window_ok(lo, hi, a.Z) ? hi - lo + 1 : 0;
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r)
+        if (r < w) cp_async4(&st.P[r][lane], N + (int64_t)(lo + r) * ld + c);
+    }
+    cp_async_commit();
+  };
+
+  int scount = 0;  // entries in the stiff list (warp-uniform)
+  issue_front(0);
+  issue_front(1);
+  cp_async_wait<1>();  // front(0)
+  __syncwarp();
+  issue_planes(0);
+  for (int k = 0; k < K; ++k) {
+    issue_front(k + 2);
+    cp_async_wait<2>();  // front(k+1): pending are planes(k), front(k+2)
+    __syncwarp();
+    issue_planes(k + 1);
+    cp_async_wait<2>();  // planes(k): pending are front(k+2), planes(k+1)
+    __syncwarp();
+
+    const ChunkStage& st = S.st[k % kStages];
+    const int c = ((gw + k * TW) << 5) + lane;
+    const float Ec = st.E[lane];
+    const int lo = st.lo[lane], hi = st.hi[lane];
+    const bool ok = window_ok(lo, hi, a.Z);
+    if (!ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
+    const int WMw = __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
+    bool stiff = false;
     if (ok) {
       switch (WMw) {
         case 1:
-          hard = easy_cell<1>(a, tab, c, Ec, lo, hi);
+          stiff = easy_cell<1>(a, tab, st, lane, c, Ec, lo, hi);
           break;
         case 2:
-          hard = easy_cell<2>(a, tab, c, Ec, lo, hi);
+          stiff = easy_cell<2>(a, tab, st, lane, c, Ec, lo, hi);
           break;
         case 3:
-          hard = easy_cell<3>(a, tab, c, Ec, lo, hi);
+          stiff = easy_cell<3>(a, tab, st, lane, c, Ec, lo, hi);
           break;
         case 4:
-          hard = easy_cell<4>(a, tab, c, Ec, lo, hi);
+          stiff = easy_cell<4>(a, tab, st, lane, c, Ec, lo, hi);
           break;
         case 5:
-          hard = easy_cell<5>(a, tab, c, Ec, lo, hi);
+          stiff = easy_cell<5>(a, tab, st, lane, c, Ec, lo, hi);
           break;
         default:
-          hard = easy_cell<6>(a, tab, c, Ec, lo, hi);
+          stiff = easy_cell<6>(a, tab, st, lane, c, Ec, lo, hi);
           break;
       }
     }
-    warp_append(&a.hdr[kHdrHard], a.hard, hard, (uint32_t)c);
-  }
-}
-
-// The hard cells, one per thread, each with its own width.
-__global__ void __launch_bounds__(kThreads)
-    ion_step_f32_hard_kernel(const __grid_constant__ StepArgs a) {
-  __shared__ StagedF32 tab;
-  stage_f32(a.tab, a.log2dt, &tab);
-  __syncthreads();
-  const unsigned n = *((volatile unsigned*)&a.hdr[kHdrHard]);
-  const unsigned stride = gridDim.x * blockDim.x;
-  const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
-    const bool in = i < n;
-    const int c = in ? (int)a.hard[i] : 0;
-    const int lo = in ? a.lo[c] : 0, hi = in ? a.hi[c] : 0;
-    const float Ec = in ? static_cast<const float*>(a.E)[c] : 0.0f;
-    bool fb = false;
-    if (in) {
-      switch (hi - lo + 1) {
-        case 2:
-          fb = cell<F32Form, 2>(a, tab, c, Ec, lo, hi, true);
-          break;
-        case 3:
-          fb = cell<F32Form, 3>(a, tab, c, Ec, lo, hi, true);
-          break;
-        case 4:
-          fb = cell<F32Form, 4>(a, tab, c, Ec, lo, hi, true);
-          break;
-        case 5:
-          fb = cell<F32Form, 5>(a, tab, c, Ec, lo, hi, true);
-          break;
-        case 6:
-          fb = cell<F32Form, 6>(a, tab, c, Ec, lo, hi, true);
-          break;
-        default:
-          break;
+    // stiff cells: copy their inputs into the list
+    const unsigned m = __ballot_sync(kFull, stiff);
+    if (m) {
+      if (stiff) {
+        const int e = scount + __popc(m & ((1u << lane) - 1u));
+        S.sl.E[e] = Ec;
+        S.sl.c[e] = c;
+        S.sl.lo[e] = (uint8_t)lo;
+        S.sl.hi[e] = (uint8_t)hi;
+        const int w = hi - lo + 1;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r)
+          if (r < w) S.sl.V[r][e] = st.P[r][lane];
       }
+      scount += __popc(m);
+      __syncwarp();
+      if (scount >= 32) {
+        drain_stiff(a, tab, S.sl, scount - 32, 32, lane);
+        scount -= 32;
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+  if (scount > 0) drain_stiff(a, tab, S.sl, 0, scount, lane);
+
+  // the last, partial chunk (ncells % 32 cells) goes to one warp
+  const int tail = a.ncells & 31;
+  if (tail && gw == TW - 1) {
+    const int c = (nfull << 5) + lane;
+    bool fb = false;
+    if (lane < tail) {
+      const float Ec = E[c];
+      const int lo = a.lo[c], hi = a.hi[c];
+      if (!window_ok(lo, hi, a.Z))
+        atomicAdd(&a.hdr[kHdrInvalid], 1u);
+      else
+        fb = global_cell_any<F32Form>(a, tab, c, Ec, lo, hi, true);
     }
     warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
   }
 }
 
+// ---------------------------------------------------------------------------
+// Plain FP64 form: one cell per thread, all paths inline.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
     ion_step_f64_kernel(const __grid_constant__ StepArgs a) {
   __shared__ StagedF64 tab;
   stage_f64(a.tab, a.log2dt, &tab);
   __syncthreads();
   const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = cl < a.ncells;
-  const int c = in ? (int)cl : 0;
-  double Ec;
-  int lo, hi;
-  bool ok;
-  const int WMw = load_cell<F64Form>(a, c, in, Ec, lo, hi, ok);
-  if (in && !ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
-  cell_bucket<F64Form, 1, 6>(WMw, a, tab, c, Ec, lo, hi, ok, false);
+  if (cl >= a.ncells) return;
+  const int c = (int)cl;
+  const double Ec = static_cast<const double*>(a.E)[c];
+  const int lo = a.lo[c], hi = a.hi[c];
+  if (!window_ok(lo, hi, a.Z)) {
+    atomicAdd(&a.hdr[kHdrInvalid], 1u);
+    return;
+  }
+  global_cell_any<F64Form>(a, tab, c, Ec, lo, hi, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -363,47 +504,41 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-}  // namespace
-
-size_t step_workspace_bytes(int64_t ncells, bool f64) {
-  if (f64) return kHdrBytes;
-  const size_t q = (4 * (size_t)ncells + 255) / 256 * 256;
-  return kHdrBytes + 2 * q;
-}
-
-void bind_workspace(StepArgs& a, void* ws) {
-  char* p = static_cast<char*>(ws);
-  a.hdr = reinterpret_cast<uint32_t*>(p);
-  const size_t q = (4 * (size_t)a.ncells + 255) / 256 * 256;
-  a.queue = reinterpret_cast<uint32_t*>(p + kHdrBytes);
-  a.hard = reinterpret_cast<uint32_t*>(p + kHdrBytes + q);
-}
-
-namespace {
 int resident_blocks_f32() {
   static int blocks = 0;
   if (!blocks) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ion_step_f32_kernel, kThreads, 0) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ion_step_f32_kernel, kWarps * 32,
+                                                      0) != cudaSuccess ||
         b < 1)
       b = 1;
     blocks = b;
   }
   return blocks;
 }
+
 }  // namespace
+
+size_t step_workspace_bytes(int64_t ncells, bool f64) {
+  if (f64) return kHdrBytes;
+  return kHdrBytes + (4 * (size_t)ncells + 255) / 256 * 256;
+}
+
+void bind_workspace(StepArgs& a, void* ws) {
+  char* p = static_cast<char*>(ws);
+  a.hdr = reinterpret_cast<uint32_t*>(p);
+  a.queue = reinterpret_cast<uint32_t*>(p + kHdrBytes);
+}
 
 cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   if (a.ncells == 0) return cudaSuccess;
-  const int64_t tiles = (a.ncells + kThreads - 1) / kThreads;
+  const int64_t chunks = ((int64_t)a.ncells + 31) / 32;
+  const int64_t need = (chunks + kWarps - 1) / kWarps;
   const int64_t cap = (int64_t)resident_blocks_f32() * num_sms;
-  const int blocks = (int)(tiles < cap ? tiles : cap);
-  ion_step_f32_kernel<<<blocks, kThreads, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ion_step_f32_hard_kernel<<<4 * num_sms, kThreads, 0, s>>>(a);
+  const int blocks = (int)(need < cap ? need : cap);
+  ion_step_f32_kernel<<<blocks, kWarps * 32, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const bool need_fb = (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
                        ((a.flags & ION_FORCE_FP64_COEF) != 0 || a.gap > 0.0);

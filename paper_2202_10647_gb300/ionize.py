@@ -235,6 +235,6 @@ def counters(ws: torch.Tensor):
 
 
 def stiff_cells(ws: torch.Tensor) -> int:
-    """Cells the last FP32 step that used `ws` finished in its second kernel
-    (some W dt > 0.025); synchronizes."""
+    """Cells of the last FP32 step that used `ws` with some W dt > 0.025,
+    finished on the long path; synchronizes."""
     return int(ws[8:12].cpu().view(torch.int32)[0])

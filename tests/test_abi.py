@@ -60,7 +60,7 @@ def test_host_side_rejections():
 
 def test_workspace_sizes():
     assert ionize.workspace_bytes(0) == 256
-    # header + two queues of one slot per cell
+    # header + a queue of one slot per cell
     for n in (1, 31, 32, 1000, 33554432):
-        assert 256 + 8 * n <= ionize.workspace_bytes(n) <= 768 + 8 * n
+        assert 256 + 4 * n <= ionize.workspace_bytes(n) <= 512 + 4 * n
     assert ionize.workspace_bytes(1000, ionize.ION_F64_PLAIN) == 256

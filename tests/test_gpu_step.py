@@ -224,7 +224,7 @@ def test_guard_planes_untouched():
     n = wl.ncells
     dev = "cuda"
     Z = 7
-    guard = 13
+    guard = 12
     big = torch.full((Z + 3, n + 2 * guard), 12345.0, device=dev)
     big[1:Z + 2, guard:guard + n] = wl.N[:, :n].to(dev)
     # view with ld = n + 2*guard starting at plane 1, cell `guard`
