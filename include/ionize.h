@@ -119,8 +119,10 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
               int k_hi, void* W_out, int64_t ldw, int dtype, void* stream);
 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
- * a 256-byte header plus, for ION_F32, a queue of one 4-byte slot per cell
- * (cells whose Bateman coefficients are computed in FP64). */
+ * a 256-byte header plus, for ION_F32, 38 bytes per cell: a 4-byte queue
+ * slot (cells whose Bateman coefficients are computed in FP64) and a 34-byte
+ * record (cells with a rate W dt > 0.025, finished by a second kernel from
+ * the inputs the first one loaded). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
 
 /* ion_step -- advance the charge-state populations of every cell by one

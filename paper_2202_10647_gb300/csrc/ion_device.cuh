@@ -35,9 +35,8 @@ constexpr double kEmin = 1e-6;
 // FP32 copy of the table staged in shared memory, each double held as an
 // unevaluated sum hi + lo of two floats, with log2(dt) folded into a.
 struct StagedF32 {
-  float a_hi[ION_MAX_Z + 1], a_lo[ION_MAX_Z + 1];
-  float b_hi[ION_MAX_Z + 1], b_lo[ION_MAX_Z + 1];
-  float C_hi[ION_MAX_Z + 1], C_lo[ION_MAX_Z + 1];
+  float4 hi[ION_MAX_Z + 1];  // {a_hi, b_hi, C_hi, a_lo}: one 16-byte load
+  float2 lo[ION_MAX_Z + 1];  // {b_lo, C_lo}
 };
 
 struct StagedF64 {
@@ -56,9 +55,12 @@ __device__ __forceinline__ void stage_f32(const SpeciesTable* t, double log2dt,
                                           StagedF32* s) {
   const int Z = t->Z;
   for (int k = threadIdx.x; k < Z; k += blockDim.x) {
-    split_f64(t->a2[k] + log2dt, s->a_hi[k], s->a_lo[k]);
-    split_f64(t->b[k], s->b_hi[k], s->b_lo[k]);
-    split_f64(t->C[k], s->C_hi[k], s->C_lo[k]);
+    float ah, al, bh, bl, ch, cl;
+    split_f64(t->a2[k] + log2dt, ah, al);
+    split_f64(t->b[k], bh, bl);
+    split_f64(t->C[k], ch, cl);
+    s->hi[k] = make_float4(ah, bh, ch, al);
+    s->lo[k] = make_float2(bl, cl);
   }
 }
 
@@ -124,22 +126,21 @@ template <bool Precise = false>
 __device__ __forceinline__ float rate_dt_f32(const StagedF32& t, int k,
                                              const FieldF32& f) {
   if (f.zero) return 0.0f;
-  const float Ch = t.C_hi[k];
-  const float q = Ch * f.rE;
+  const float4 h = t.hi[k];  // a_hi, b_hi, C_hi, a_lo
+  const float q = h.z * f.rE;
   if (q > (float)kCutoffLog2) return 0.0f;
-  const float bh = t.b_hi[k];
   if (!Precise) {
-    const float y0 = fmaf(-bh, f.lg, t.a_hi[k]) - q;
+    const float y0 = fmaf(-h.y, f.lg, h.x) - q;
     if (y0 < -12.0f) return ex2_approx(y0);
   }
-  const float ql = (fmaf(-q, f.E, Ch) + t.C_lo[k]) * f.rE;  // C/E = q + ql
-  const float p = bh * f.ex;
-  const float pe = fmaf(bh, f.ex, -p);  // b_hi*ex = p + pe exactly
+  const float2 l = t.lo[k];  // b_lo, C_lo
+  const float ql = (fmaf(-q, f.E, h.z) + l.y) * f.rE;  // C/E = q + ql
+  const float p = h.y * f.ex;
+  const float pe = fmaf(h.y, f.ex, -p);  // b_hi*ex = p + pe exactly
   float s1, e1, s2, e2;
-  two_sum(t.a_hi[k], -p, s1, e1);
+  two_sum(h.x, -p, s1, e1);
   two_sum(s1, -q, s2, e2);
-  const float small =
-      ((t.a_lo[k] - pe) - ql) - fmaf(bh, f.lm, t.b_lo[k] * f.lg);
+  const float small = ((h.w - pe) - ql) - fmaf(h.y, f.lm, l.x * f.lg);
   const float tail = (e1 + e2) + small;
   if (Precise) {
     // 2^(s2 + tail) as 2^s2 2^tail keeps the relative error at a few ulp for

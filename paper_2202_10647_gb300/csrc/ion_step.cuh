@@ -12,7 +12,7 @@ namespace ion {
 // Workspace header (uint32 words at the start of the workspace).
 constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
 constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
-constexpr int kHdrStiff = 2;     // cells finished through the per-warp stiff lists
+constexpr int kHdrStiff = 2;     // stiff-cell records written by the streaming kernel
 constexpr int kHdrWords = 3;
 constexpr size_t kHdrBytes = 256;
 
@@ -34,6 +34,13 @@ struct StepArgs {
   int flags;
   uint32_t* hdr;    // workspace header (kHdr* words)
   uint32_t* queue;  // cells for the FP64-coefficient kernel
+  // stiff-cell records (FP32 form): cell, |E|, lo | hi << 8, window planes
+  // rec_V[r * rec_cap + i]
+  uint32_t* rec_c;
+  float* rec_E;
+  uint16_t* rec_lohi;
+  float* rec_V;
+  int64_t rec_cap;
 };
 
 // Workspace layout (step.cu).

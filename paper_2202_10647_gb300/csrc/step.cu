@@ -1,19 +1,22 @@
 // step.cu -- the ion_step kernels.
 //
-// FP32 form (ION_F32), two kernels on the caller's stream:
+// FP32 form (ION_F32), three kernels on the caller's stream:
 //   ion_step_f32_kernel  persistent; every warp walks its own sequence of
 //       32-cell chunks through a 4-stage ring in shared memory.  cp.async
 //       brings |E|, k_lo and k_hi in two chunks ahead and each lane's own
-//       window planes one chunk ahead, so the loads in flight do not cost
+//       window planes one chunk ahead, so the loads in flight cost no
 //       registers and the traffic is exactly the cells' windows.  A cell
-//       whose rates all have W dt <= 0.025 is finished at once (at most four
-//       Taylor terms of exp(dt A)); the others ("stiff" cells) are copied with
-//       their inputs into a per-warp list in shared memory and finished 32 at
-//       a time, so the long paths run in full warps.  (In a laser field |E|
-//       swings from zero to its peak every few cells, so most warps near the
-//       pulse hold a few stiff cells.)  Stiff cells take the Taylor form up to
-//       W dt <= 1 and the divided-difference (Bateman) form above; cells with
-//       a nearly degenerate rate pair are left untouched and queued for
+//       whose rates all have W dt <= 0.025 is finished here (at most four
+//       Taylor terms of exp(dt A)).  The others ("stiff" cells) write the
+//       inputs already loaded into a record queue (coalesced, warp by warp):
+//       in a laser field |E| swings from zero to its peak every few cells, so
+//       most warps near the pulse hold a few stiff cells, and finishing them
+//       in place would make every such warp run the longest path of its
+//       lanes and would size this kernel's registers for it.
+//   ion_step_f32_stiff_kernel  the records, one per thread in full warps:
+//       Taylor form up to W dt <= 1, divided-difference (Bateman) form above.
+//       Cells with a nearly degenerate rate pair are left untouched and
+//       queued for
 //   ion_step_fb_kernel   FP32 rates, FP64 Bateman coefficients and
 //       propagation, rounded back to FP32.
 // Plain FP64 form (ION_F64_PLAIN): ion_step_f64_kernel, one cell per thread,
@@ -33,7 +36,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;       // FP64 kernel
 constexpr int kWarps = 4;           // warps per block of the FP32 kernel
 constexpr int kStages = 4;          // chunks in the per-warp ring
-constexpr int kStiffCap = 64;       // per-warp list of stiff cells
 constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms
 constexpr int kEasyTerms = 4;
 
@@ -184,7 +186,7 @@ __device__ __forceinline__ bool global_cell_any(const StepArgs& a,
 }
 
 // ---------------------------------------------------------------------------
-// FP32 streaming kernel: per-warp shared memory.
+// FP32 streaming kernel.
 // ---------------------------------------------------------------------------
 struct ChunkStage {
   float E[32];
@@ -193,18 +195,26 @@ struct ChunkStage {
   float P[ION_MAX_WINDOW][32];  // P[r][lane] = N[lo + r] of the lane's cell
 };
 
-struct StiffList {
-  float E[kStiffCap];
-  int c[kStiffCap];
-  uint8_t lo[kStiffCap];
-  uint8_t hi[kStiffCap];
-  float V[ION_MAX_WINDOW][kStiffCap];
-};
-
-struct WarpSmem {
-  ChunkStage st[kStages];
-  StiffList sl;
-};
+// Appends the record of a stiff cell (one atomic per warp).  Every lane of
+// the warp calls this; `take` lanes pass their cell's inputs.
+__device__ __forceinline__ void append_record(const StepArgs& a, bool take, int c,
+                                              float Ec, int lo, int hi,
+                                              const float* v, int vstride) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(&a.hdr[kHdrStiff], (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, 0);
+  if (take) {
+    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
+    a.rec_c[i] = (uint32_t)c;
+    a.rec_E[i] = Ec;
+    a.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
+    const int w = hi - lo + 1;
+    for (int r = 0; r < w; ++r) a.rec_V[(int64_t)r * a.rec_cap + i] = v[r * vstride];
+  }
+}
 
 // Easy path of a lane's cell in a staged chunk: finishes it if every
 // W dt <= kLamEasy and returns false, else returns true untouched.
@@ -212,8 +222,6 @@ template <int WM>
 __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& tab,
                                           const ChunkStage& st, int lane, int c,
                                           float Ec, int lo, int hi) {
-  float* __restrict__ N = static_cast<float*>(a.N);
-  const int64_t ld = a.ld;
   const int w = hi - lo + 1;
   float v[WM];
 #pragma unroll
@@ -234,9 +242,12 @@ __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& ta
       dne = taylor_propagate<float, WM, kEasyTerms>(v, lam, w, lmax);
       if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
         slide_window<float, WM>(v, w, a.Z, (float)a.eps, nlo, nhi);
+      float* p = static_cast<float*>(a.N) + (int64_t)lo * a.ld + c;
 #pragma unroll
-      for (int r = 0; r < WM; ++r)
-        if (r < w) __stcs(N + (int64_t)(lo + r) * ld + c, v[r]);
+      for (int r = 0; r < WM; ++r) {
+        if (r < w) __stcs(p, v[r]);
+        p += a.ld;
+      }
     }
   }
   const float* __restrict__ G = static_cast<const float*>(a.n_gas);
@@ -248,56 +259,16 @@ __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& ta
   return false;
 }
 
-// Finishes `cnt` (<= 32) entries of the stiff list starting at `first`, one
-// per lane.  Every lane of the warp calls this.
-__device__ __forceinline__ void drain_stiff(const StepArgs& a, const StagedF32& tab,
-                                            const StiffList& sl, int first, int cnt,
-                                            int lane) {
-  bool fb = false;
-  int c = 0;
-  if (lane == 0) atomicAdd(&a.hdr[kHdrStiff], (unsigned)cnt);
-  if (lane < cnt) {
-    const int e = first + lane;
-    c = sl.c[e];
-    const int lo = sl.lo[e], hi = sl.hi[e];
-    const float Ec = sl.E[e];
-    switch (hi - lo + 1) {
-      case 2: {
-        float v[2] = {sl.V[0][e], sl.V[1][e]};
-        fb = finish_cell<F32Form, 2>(a, tab, c, Ec, lo, hi, v, true);
-      } break;
-      case 3: {
-        float v[3] = {sl.V[0][e], sl.V[1][e], sl.V[2][e]};
-        fb = finish_cell<F32Form, 3>(a, tab, c, Ec, lo, hi, v, true);
-      } break;
-      case 4: {
-        float v[4] = {sl.V[0][e], sl.V[1][e], sl.V[2][e], sl.V[3][e]};
-        fb = finish_cell<F32Form, 4>(a, tab, c, Ec, lo, hi, v, true);
-      } break;
-      case 5: {
-        float v[5] = {sl.V[0][e], sl.V[1][e], sl.V[2][e], sl.V[3][e], sl.V[4][e]};
-        fb = finish_cell<F32Form, 5>(a, tab, c, Ec, lo, hi, v, true);
-      } break;
-      default: {
-        float v[6] = {sl.V[0][e], sl.V[1][e], sl.V[2][e],
-                      sl.V[3][e], sl.V[4][e], sl.V[5][e]};
-        fb = finish_cell<F32Form, 6>(a, tab, c, Ec, lo, hi, v, true);
-      } break;
-    }
-  }
-  warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
-}
-
-__global__ void __launch_bounds__(kWarps * 32, 4)
+__global__ void __launch_bounds__(kWarps * 32, 8)
     ion_step_f32_kernel(const __grid_constant__ StepArgs a) {
   __shared__ StagedF32 tab;
-  __shared__ WarpSmem wsm[kWarps];
+  __shared__ ChunkStage ring[kWarps][kStages];
   stage_f32(a.tab, a.log2dt, &tab);
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  WarpSmem& S = wsm[wib];
+  ChunkStage* S = ring[wib];
   const int gw = blockIdx.x * kWarps + wib;
   const int TW = gridDim.x * kWarps;
   const int nfull = a.ncells >> 5;
@@ -310,7 +281,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
   auto issue_front = [&](int k) {
     if (k < K) {
       const int c0 = (gw + k * TW) << 5;
-      ChunkStage& st = S.st[k % kStages];
+      ChunkStage& st = S[k % kStages];
       cp_async4(&st.E[lane], E + c0 + lane);
       if (lane < 8)
         cp_async4(&st.lo[4 * lane], a.lo + c0 + 4 * lane);
@@ -323,17 +294,18 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
   auto issue_planes = [&](int k) {
     if (k < K) {
       const int c = ((gw + k * TW) << 5) + lane;
-      ChunkStage& st = S.st[k % kStages];
+      ChunkStage& st = S[k % kStages];
       const int lo = st.lo[lane], hi = st.hi[lane];
       const int w = window_ok(lo, hi, a.Z) ? hi - lo + 1 : 0;
-#pragma unroll
-      for (int r = 0; r < ION_MAX_WINDOW; ++r)
-        if (r < w) cp_async4(&st.P[r][lane], N + (int64_t)(lo + r) * ld + c);
+      const float* p = N + (int64_t)lo * ld + c;
+      for (int r = 0; r < w; ++r) {
+        cp_async4(&st.P[r][lane], p);
+        p += ld;
+      }
     }
     cp_async_commit();
   };
 
-  int scount = 0;  // entries in the stiff list (warp-uniform)
   issue_front(0);
   issue_front(1);
   cp_async_wait<1>();  // front(0)
@@ -347,7 +319,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     cp_async_wait<2>();  // planes(k): pending are front(k+2), planes(k+1)
     __syncwarp();
 
-    const ChunkStage& st = S.st[k % kStages];
+    const ChunkStage& st = S[k % kStages];
     const int c = ((gw + k * TW) << 5) + lane;
     const float Ec = st.E[lane];
     const int lo = st.lo[lane], hi = st.hi[lane];
@@ -356,66 +328,92 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     const int WMw = __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
     bool stiff = false;
     if (ok) {
-      switch (WMw) {
-        case 1:
-          stiff = easy_cell<1>(a, tab, st, lane, c, Ec, lo, hi);
-          break;
-        case 2:
-          stiff = easy_cell<2>(a, tab, st, lane, c, Ec, lo, hi);
-          break;
-        case 3:
-          stiff = easy_cell<3>(a, tab, st, lane, c, Ec, lo, hi);
-          break;
-        case 4:
-          stiff = easy_cell<4>(a, tab, st, lane, c, Ec, lo, hi);
-          break;
-        case 5:
-          stiff = easy_cell<5>(a, tab, st, lane, c, Ec, lo, hi);
-          break;
-        default:
-          stiff = easy_cell<6>(a, tab, st, lane, c, Ec, lo, hi);
-          break;
-      }
+      if (WMw <= 1)
+        stiff = easy_cell<1>(a, tab, st, lane, c, Ec, lo, hi);
+      else if (WMw == 2)
+        stiff = easy_cell<2>(a, tab, st, lane, c, Ec, lo, hi);
+      else if (WMw <= 4)
+        stiff = easy_cell<4>(a, tab, st, lane, c, Ec, lo, hi);
+      else
+        stiff = easy_cell<6>(a, tab, st, lane, c, Ec, lo, hi);
     }
-    // stiff cells: copy their inputs into the list
-    const unsigned m = __ballot_sync(kFull, stiff);
-    if (m) {
-      if (stiff) {
-        const int e = scount + __popc(m & ((1u << lane) - 1u));
-        S.sl.E[e] = Ec;
-        S.sl.c[e] = c;
-        S.sl.lo[e] = (uint8_t)lo;
-        S.sl.hi[e] = (uint8_t)hi;
-        const int w = hi - lo + 1;
-#pragma unroll
-        for (int r = 0; r < ION_MAX_WINDOW; ++r)
-          if (r < w) S.sl.V[r][e] = st.P[r][lane];
-      }
-      scount += __popc(m);
-      __syncwarp();
-      if (scount >= 32) {
-        drain_stiff(a, tab, S.sl, scount - 32, 32, lane);
-        scount -= 32;
-      }
-    }
+    append_record(a, stiff, c, Ec, lo, hi, &st.P[0][lane], 32);
     __syncwarp();
   }
   cp_async_wait<0>();
-  __syncwarp();
-  if (scount > 0) drain_stiff(a, tab, S.sl, 0, scount, lane);
 
-  // the last, partial chunk (ncells % 32 cells) goes to one warp
+  // the last, partial chunk (ncells % 32 cells): every valid cell becomes a
+  // record for the stiff kernel, which runs the full path
   const int tail = a.ncells & 31;
   if (tail && gw == TW - 1) {
     const int c = (nfull << 5) + lane;
-    bool fb = false;
+    bool take = false;
+    float Ec = 0.0f, v[ION_MAX_WINDOW];
+    int lo = 0, hi = 0;
     if (lane < tail) {
-      const float Ec = E[c];
-      const int lo = a.lo[c], hi = a.hi[c];
-      if (!window_ok(lo, hi, a.Z))
-        atomicAdd(&a.hdr[kHdrInvalid], 1u);
-      else
-        fb = global_cell_any<F32Form>(a, tab, c, Ec, lo, hi, true);
+      Ec = E[c];
+      lo = a.lo[c];
+      hi = a.hi[c];
+      take = window_ok(lo, hi, a.Z);
+      if (!take) atomicAdd(&a.hdr[kHdrInvalid], 1u);
+      const float* p = N + (int64_t)lo * ld + c;
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+        v[r] = (take && r < hi - lo + 1) ? p[0] : 0.0f;
+        p += ld;
+      }
+    }
+    append_record(a, take, c, Ec, lo, hi, v, 1);
+  }
+}
+
+// The stiff-cell records, one per thread.
+template <int W>
+__device__ __forceinline__ bool record_cell(const StepArgs& a, const StagedF32& tab,
+                                            unsigned i, int c, float Ec, int lo,
+                                            int hi) {
+  float v[W];
+#pragma unroll
+  for (int r = 0; r < W; ++r) v[r] = __ldcs(a.rec_V + (int64_t)r * a.rec_cap + i);
+  return finish_cell<F32Form, W>(a, tab, c, Ec, lo, hi, v, true);
+}
+
+__global__ void __launch_bounds__(256)
+    ion_step_f32_stiff_kernel(const __grid_constant__ StepArgs a) {
+  __shared__ StagedF32 tab;
+  stage_f32(a.tab, a.log2dt, &tab);
+  __syncthreads();
+  const unsigned n = *((volatile unsigned*)&a.hdr[kHdrStiff]);
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
+    bool fb = false;
+    int c = 0;
+    if (i < n) {
+      c = (int)__ldcs(a.rec_c + i);
+      const float Ec = __ldcs(a.rec_E + i);
+      const unsigned lh = __ldcs(a.rec_lohi + i);
+      const int lo = lh & 0xff, hi = lh >> 8;
+      switch (hi - lo + 1) {
+        case 1:
+          fb = record_cell<1>(a, tab, i, c, Ec, lo, hi);
+          break;
+        case 2:
+          fb = record_cell<2>(a, tab, i, c, Ec, lo, hi);
+          break;
+        case 3:
+          fb = record_cell<3>(a, tab, i, c, Ec, lo, hi);
+          break;
+        case 4:
+          fb = record_cell<4>(a, tab, i, c, Ec, lo, hi);
+          break;
+        case 5:
+          fb = record_cell<5>(a, tab, i, c, Ec, lo, hi);
+          break;
+        default:
+          fb = record_cell<6>(a, tab, i, c, Ec, lo, hi);
+          break;
+      }
     }
     warp_append(&a.hdr[kHdrFallback], a.queue, fb, (uint32_t)c);
   }
@@ -519,15 +517,34 @@ int resident_blocks_f32() {
 
 }  // namespace
 
+// Workspace: header | FP64 queue (4 B/cell) | stiff records: cell index
+// (4 B), |E| (4 B), lo|hi (2 B), window (6 x 4 B) per cell.
+namespace {
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
 size_t step_workspace_bytes(int64_t ncells, bool f64) {
   if (f64) return kHdrBytes;
-  return kHdrBytes + (4 * (size_t)ncells + 255) / 256 * 256;
+  const size_t n = (size_t)ncells;
+  return kHdrBytes + round256(4 * n) + round256(4 * n) + round256(4 * n) +
+         round256(2 * n) + round256(4 * n * ION_MAX_WINDOW);
 }
 
 void bind_workspace(StepArgs& a, void* ws) {
   char* p = static_cast<char*>(ws);
+  const size_t n = (size_t)a.ncells;
   a.hdr = reinterpret_cast<uint32_t*>(p);
-  a.queue = reinterpret_cast<uint32_t*>(p + kHdrBytes);
+  p += kHdrBytes;
+  a.queue = reinterpret_cast<uint32_t*>(p);
+  p += round256(4 * n);
+  a.rec_c = reinterpret_cast<uint32_t*>(p);
+  p += round256(4 * n);
+  a.rec_E = reinterpret_cast<float*>(p);
+  p += round256(4 * n);
+  a.rec_lohi = reinterpret_cast<uint16_t*>(p);
+  p += round256(2 * n);
+  a.rec_V = reinterpret_cast<float*>(p);
+  a.rec_cap = (int64_t)n;
 }
 
 cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
@@ -539,6 +556,8 @@ cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
   const int64_t cap = (int64_t)resident_blocks_f32() * num_sms;
   const int blocks = (int)(need < cap ? need : cap);
   ion_step_f32_kernel<<<blocks, kWarps * 32, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ion_step_f32_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const bool need_fb = (a.flags & ION_NO_FP64_FALLBACK) == 0 &&
                        ((a.flags & ION_FORCE_FP64_COEF) != 0 || a.gap > 0.0);
