@@ -217,30 +217,83 @@ __device__ __forceinline__ void append_record(const StepArgs& a, bool take, int 
 }
 
 // Easy path of a lane's cell in a staged chunk: finishes it if every
-// W dt <= kLamEasy and returns false, else returns true untouched.
+// W dt <= kLamEasy and returns false, else returns true untouched.  Written
+// for lanes that mostly agree: every window rate takes the plain FP32
+// exponent, the float-float refinement runs only for rates above 2^-12, and
+// the Taylor series runs the warp's largest term count (extra terms only add
+// accuracy).
 template <int WM>
 __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& tab,
                                           const ChunkStage& st, int lane, int c,
-                                          float Ec, int lo, int hi) {
-  const int w = hi - lo + 1;
+                                          float Ec, int lo, int hi, bool ok) {
+  // every lane of the warp calls this; lanes with !ok only take part in the
+  // warp reduction
+  const int w = ok ? hi - lo + 1 : 0;
+  lo = ok ? lo : 0;
   float v[WM];
 #pragma unroll
-  for (int r = 0; r < WM; ++r) v[r] = r < w ? st.P[r][lane] : 0.0f;
+  for (int r = 0; r < WM; ++r) v[r] = st.P[r][lane];  // r >= w: ignored
   float dne = 0.0f;
   int nlo = lo, nhi = hi;
+  bool stiff = false;
   if constexpr (WM >= 2) {
-    if (w >= 2) {
-      const FieldF32 f = field_f32(Ec);
-      float lam[WM];
-      float lmax = 0.0f;
+    const FieldF32 f = field_f32(Ec);
+    const bool live = w >= 2 && !f.zero && !a.zero_dt;
+    float lam[WM];
+    float y0[WM];
+    bool need_precise = false;
 #pragma unroll
-      for (int r = 0; r < WM; ++r) {
-        lam[r] = (r < w - 1 && !a.zero_dt) ? rate_dt_f32(tab, lo + r, f) : 0.0f;
-        lmax = fmaxf(lmax, lam[r]);
+    for (int r = 0; r < WM - 1; ++r) {
+      const float4 h = tab.hi[min(lo + r, ION_MAX_Z)];
+      const float q = h.z * f.rE;
+      y0[r] = fmaf(-h.y, f.lg, h.x) - q;
+      const bool on = live && r < w - 1 && q <= (float)kCutoffLog2;
+      lam[r] = on ? ex2_approx(y0[r]) : 0.0f;
+      need_precise |= on && y0[r] >= -12.0f;
+    }
+    lam[WM - 1] = 0.0f;
+    if (need_precise) {
+#pragma unroll
+      for (int r = 0; r < WM - 1; ++r)
+        if (lam[r] != 0.0f && y0[r] >= -12.0f) lam[r] = rate_dt_f32(tab, lo + r, f);
+    }
+    float lmax = 0.0f;
+#pragma unroll
+    for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[r]);
+    stiff = lmax > kLamEasy;
+    // terms of exp(dt A) v: R = number of thresholds below 2 lmax (<= 4)
+    const float x = stiff ? 0.0f : 2.0f * lmax;
+    int R = 0;
+#pragma unroll
+    for (int i = 0; i < kEasyTerms; ++i) R += x > kThrF32[i] ? 1 : 0;
+    const int Rw = __reduce_max_sync(kFull, R);
+    if (!stiff && w >= 2) {
+      float t[WM], inc[WM];
+#pragma unroll
+      for (int i = 0; i < WM; ++i) {
+        t[i] = i < w ? v[i] : 0.0f;
+        inc[i] = 0.0f;
       }
-      if (lmax > kLamEasy) return true;
-      dne = taylor_propagate<float, WM, kEasyTerms>(v, lam, w, lmax);
-      if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
+#pragma unroll
+      for (int k = 1; k <= kEasyTerms; ++k) {
+        if (k > Rw) break;
+        const float rk = 1.0f / k;
+#pragma unroll
+        for (int i = WM - 1; i >= 0; --i) {
+          const float gain = i > 0 ? lam[i - 1] * t[i - 1] : 0.0f;
+          t[i] = (gain - lam[i] * t[i]) * rk;
+          inc[i] += t[i];
+        }
+      }
+      float cum = 0.0f;
+#pragma unroll
+      for (int r = 0; r < WM - 1; ++r) {
+        cum -= r < w - 1 ? inc[r] : 0.0f;  // population that left states <= r
+        dne += cum;
+      }
+#pragma unroll
+      for (int r = 0; r < WM; ++r) v[r] += inc[r];
+      if ((a.flags & ION_NO_WINDOW_UPDATE) == 0 && v[0] < (float)a.eps && hi < a.Z)
         slide_window<float, WM>(v, w, a.Z, (float)a.eps, nlo, nhi);
       float* p = static_cast<float*>(a.N) + (int64_t)lo * a.ld + c;
 #pragma unroll
@@ -250,6 +303,7 @@ __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& ta
       }
     }
   }
+  if (stiff || !ok) return stiff;
   const float* __restrict__ G = static_cast<const float*>(a.n_gas);
   __stcs(static_cast<float*>(a.dne) + c, G ? dne * G[c] : dne);
   if (nlo != lo) {
@@ -264,6 +318,13 @@ __global__ void __launch_bounds__(kWarps * 32, 8)
   __shared__ StagedF32 tab;
   __shared__ ChunkStage ring[kWarps][kStages];
   stage_f32(a.tab, a.log2dt, &tab);
+  {
+    // plane slots past a cell's window are read (and ignored) by the easy
+    // path; keep them finite
+    float* z = reinterpret_cast<float*>(&ring[0][0]);
+    for (int i = threadIdx.x; i < (int)(sizeof(ring) / sizeof(float)); i += blockDim.x)
+      z[i] = 0.0f;
+  }
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -326,17 +387,15 @@ __global__ void __launch_bounds__(kWarps * 32, 8)
     const bool ok = window_ok(lo, hi, a.Z);
     if (!ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
     const int WMw = __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
-    bool stiff = false;
-    if (ok) {
-      if (WMw <= 1)
-        stiff = easy_cell<1>(a, tab, st, lane, c, Ec, lo, hi);
-      else if (WMw == 2)
-        stiff = easy_cell<2>(a, tab, st, lane, c, Ec, lo, hi);
-      else if (WMw <= 4)
-        stiff = easy_cell<4>(a, tab, st, lane, c, Ec, lo, hi);
-      else
-        stiff = easy_cell<6>(a, tab, st, lane, c, Ec, lo, hi);
-    }
+    bool stiff;
+    if (WMw <= 1)
+      stiff = easy_cell<1>(a, tab, st, lane, c, Ec, lo, hi, ok);
+    else if (WMw == 2)
+      stiff = easy_cell<2>(a, tab, st, lane, c, Ec, lo, hi, ok);
+    else if (WMw <= 4)
+      stiff = easy_cell<4>(a, tab, st, lane, c, Ec, lo, hi, ok);
+    else
+      stiff = easy_cell<6>(a, tab, st, lane, c, Ec, lo, hi, ok);
     append_record(a, stiff, c, Ec, lo, hi, &st.P[0][lane], 32);
     __syncwarp();
   }
