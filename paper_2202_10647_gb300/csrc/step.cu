@@ -288,8 +288,10 @@ __device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& ta
       float cum = 0.0f;
 #pragma unroll
       for (int r = 0; r < WM - 1; ++r) {
-        cum -= r < w - 1 ? inc[r] : 0.0f;  // population that left states <= r
-        dne += cum;
+        if (r < w - 1) {
+          cum -= inc[r];  // population that left states <= r
+          dne += cum;
+        }
       }
 #pragma unroll
       for (int r = 0; r < WM; ++r) v[r] += inc[r];
