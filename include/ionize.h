@@ -171,6 +171,38 @@ ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
              void* dne, const void* n_gas, const ion_step_opts* opts, int flags,
              void* workspace, size_t workspace_bytes, void* stream);
 
+/* ion_step_noalloc -- ion_step for callers that cannot allocate device
+ * memory.  Some callers cannot make a device allocation at the point where
+ * they step the populations: code that runs while a CUDA graph is being
+ * captured by someone else, plugins whose host forbids device allocations
+ * of its guests, or codes that fix their memory footprint at start-up.  This
+ * entry point takes the same arguments as ion_step minus the workspace, and
+ * uses instead a scratch array that is a file-scope __device__ variable of
+ * this library: ION_STEP_NOALLOC_SCRATCH_BYTES (about 9.5 MB) on every GPU
+ * that loads the library, held until the process exits.  The paper has no
+ * counterpart of this call.
+ *   - ncells <= ION_STEP_NOALLOC_MAX_CELLS (262144); larger calls return
+ *     ION_EINVAL (split the cells into ranges: offset E, N, k_lo, k_hi, dne
+ *     and n_gas by the first cell of the range and keep ld).
+ *   - It allocates nothing and frees nothing.  The first call on a device
+ *     looks up the device address of the array (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the contents
+ *     the last call left; the counters a step needs zeroed are reset by the
+ *     step itself.  Calls that overlap on the device (other streams, other
+ *     host threads) race on the array: serialize them.
+ *   - After the call the array holds the workspace header described for
+ *     ion_step; it is not readable through this interface.
+ * Errors: those of ion_step, plus ION_EINVAL for ncells beyond the maximum
+ * and ION_ECUDA if the array's address cannot be obtained. */
+#define ION_STEP_NOALLOC_MAX_CELLS 262144
+#define ION_STEP_NOALLOC_SCRATCH_BYTES 9961728
+ION_API int ion_step_noalloc(const ion_species* sp, const void* E, void* N,
+                             int64_t ld, int64_t ncells, double dt_fs,
+                             uint8_t* k_lo, uint8_t* k_hi, void* dne,
+                             const void* n_gas, const ion_step_opts* opts,
+                             int flags, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 ION_API const char* ion_last_error(void);
 

@@ -113,6 +113,16 @@ int check_species(const ion_species* sp) {
 
 }  // namespace
 
+int ion::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 extern "C" {
 
 const char* ion_last_error(void) { return g_err.c_str(); }

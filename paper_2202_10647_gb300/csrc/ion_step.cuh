@@ -47,6 +47,10 @@ struct StepArgs {
 size_t step_workspace_bytes(int64_t ncells, bool f64);
 void bind_workspace(StepArgs& a, void* ws);
 
+// Sets the calling thread's ion_last_error() message and returns `code`
+// (api.cu).
+int set_error(int code, const char* fmt, ...);
+
 // Launchers (step.cu).  They only enqueue; the caller has validated.
 cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs& a, cudaStream_t s);

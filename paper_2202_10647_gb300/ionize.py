@@ -35,7 +35,11 @@ ION_MAX_WINDOW = 6
 
 #: every symbol include/ionize.h declares
 EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
-           "ion_rates", "ion_step_workspace_bytes", "ion_step", "ion_last_error")
+           "ion_rates", "ion_step_workspace_bytes", "ion_step", "ion_step_noalloc",
+           "ion_last_error")
+
+#: largest ncells of one ion_step_noalloc call
+ION_STEP_NOALLOC_MAX_CELLS = 262144
 
 _lock = threading.Lock()
 _lib = None
@@ -81,6 +85,9 @@ def _declare(lib):
     lib.ion_step.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                              _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp,
                              ctypes.c_size_t, _vp]
+    lib.ion_step_noalloc.restype = ctypes.c_int
+    lib.ion_step_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
+                                     _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp]
     return lib
 
 
@@ -225,6 +232,33 @@ def step(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
                           ctypes.byref(opts), int(flags), _ptr(ws), ws.numel(),
                           _stream(E)))
     return ws
+
+
+def step_noalloc(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
+                 k_hi: torch.Tensor, dt: float, dne: torch.Tensor,
+                 n_gas: torch.Tensor | None = None, eps_shift: float = 1e-6,
+                 degen_gap: float = 1e-3, flags: int = ION_F32,
+                 ncells: int | None = None) -> None:
+    """ion_step_noalloc: the same step as `step`, with the library's own
+    fixed scratch array instead of a workspace (at most
+    ION_STEP_NOALLOC_MAX_CELLS cells per call)."""
+    f64 = bool(flags & ION_F64_PLAIN)
+    dt_ = torch.float64 if f64 else torch.float32
+    _need(E, "E", dt_)
+    dev = E.device
+    _need(N, "N", dt_, dev)
+    _need(k_lo, "k_lo", torch.uint8, dev)
+    _need(k_hi, "k_hi", torch.uint8, dev)
+    _need(dne, "dne", dt_, dev)
+    if n_gas is not None:
+        _need(n_gas, "n_gas", dt_, dev)
+    if N.dim() != 2 or N.shape[0] != sp.Z + 1:
+        raise ValueError(f"N must have shape (Z+1, ld) = ({sp.Z + 1}, ld)")
+    n = E.numel() if ncells is None else int(ncells)
+    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    _check(lib().ion_step_noalloc(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
+                                  _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
+                                  ctypes.byref(opts), int(flags), _stream(E)))
 
 
 def counters(ws: torch.Tensor):
