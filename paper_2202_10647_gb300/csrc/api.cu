@@ -275,6 +275,7 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
   a.eps = o.eps_shift;
   a.gap = o.degen_gap;
   a.flags = flags;
+  a.vec = aligned(E, 16) && aligned(N, 16) && aligned(dne, 16) && (ld % 4) == 0;
   ion::bind_workspace(a, workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = f64 ? ion::launch_step_f64(a, s) : ion::launch_step_f32(a, sp->num_sms, s);

@@ -32,6 +32,7 @@ struct StepArgs {
   double eps;
   double gap;
   int flags;
+  int vec;          // E, N 16-byte aligned and ld % 4 == 0: 16-byte copies
   uint32_t* hdr;    // workspace header (kHdr* words)
   uint32_t* queue;  // cells for the FP64-coefficient kernel
   // stiff-cell records (FP32 form): cell, |E|, lo | hi << 8, window planes

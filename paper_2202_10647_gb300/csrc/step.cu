@@ -35,7 +35,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;       // FP64 kernel
 constexpr int kWarps = 4;           // warps per block of the FP32 kernel
-constexpr int kStages = 4;          // chunks in the per-warp ring
 constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms
 constexpr int kEasyTerms = 4;
 
@@ -50,6 +49,11 @@ __device__ __forceinline__ bool window_ok(int lo, int hi, int Z) {
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -188,18 +192,22 @@ __device__ __forceinline__ bool global_cell_any(const StepArgs& a,
 // ---------------------------------------------------------------------------
 // FP32 streaming kernel.
 // ---------------------------------------------------------------------------
-struct ChunkStage {
-  float E[32];
-  uint8_t lo[32];
-  uint8_t hi[32];
-  float P[ION_MAX_WINDOW][32];  // P[r][lane] = N[lo + r] of the lane's cell
+// Each lane owns a quad of 4 consecutive cells; a warp's chunk is 128 cells.
+constexpr int kQ = 4;
+constexpr int kChunk = 32 * kQ;
+
+struct QuadStage {
+  float4 E[32];                   // |E| of the lane's quad
+  uint32_t lo[32];                // k_lo of the quad, 4 x u8
+  uint32_t hi[32];                // k_hi of the quad, 4 x u8
+  float4 P[ION_MAX_WINDOW][32];   // P[r][lane].j = N[lo_j + r] of cell j
 };
 
 // Appends the record of a stiff cell (one atomic per warp).  Every lane of
 // the warp calls this; `take` lanes pass their cell's inputs.
 __device__ __forceinline__ void append_record(const StepArgs& a, bool take, int c,
                                               float Ec, int lo, int hi,
-                                              const float* v, int vstride) {
+                                              const float* v) {
   const unsigned m = __ballot_sync(kFull, take);
   if (!m) return;
   const int lane = threadIdx.x & 31;
@@ -212,117 +220,179 @@ __device__ __forceinline__ void append_record(const StepArgs& a, bool take, int 
     a.rec_E[i] = Ec;
     a.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
     const int w = hi - lo + 1;
-    for (int r = 0; r < w; ++r) a.rec_V[(int64_t)r * a.rec_cap + i] = v[r * vstride];
+#pragma unroll
+    for (int r = 0; r < ION_MAX_WINDOW; ++r)
+      if (r < w) a.rec_V[(int64_t)r * a.rec_cap + i] = v[r];
   }
 }
 
-// Easy path of a lane's cell in a staged chunk: finishes it if every
-// W dt <= kLamEasy and returns false, else returns true untouched.  Written
-// for lanes that mostly agree: every window rate takes the plain FP32
-// exponent, the float-float refinement runs only for rates above 2^-12, and
-// the Taylor series runs the warp's largest term count (extra terms only add
-// accuracy).
+__device__ __forceinline__ float f4get(const float4& x, int j) {
+  return j == 0 ? x.x : j == 1 ? x.y : j == 2 ? x.z : x.w;
+}
+
+// Easy path of the lane's quad (cells c0..c0+3, window bound WM).  Every
+// lane of the warp calls this.  Cells whose rates all have W dt <= kLamEasy
+// are finished; stiff[j] marks the others, which are left untouched.
+// Written for lanes that mostly agree: every window rate takes the plain
+// FP32 exponent, the float-float refinement runs only for rates above 2^-12,
+// and the Taylor series runs the warp's largest term count (extra terms only
+// add accuracy).
 template <int WM>
-__device__ __forceinline__ bool easy_cell(const StepArgs& a, const StagedF32& tab,
-                                          const ChunkStage& st, int lane, int c,
-                                          float Ec, int lo, int hi, bool ok) {
-  // every lane of the warp calls this; lanes with !ok only take part in the
-  // warp reduction
-  const int w = ok ? hi - lo + 1 : 0;
-  lo = ok ? lo : 0;
-  float v[WM];
+__device__ __forceinline__ void easy_quad(const StepArgs& a, const StagedF32& tab,
+                                          const QuadStage& st, int lane, int c0,
+                                          const float (&Ev)[kQ], const int (&lo)[kQ],
+                                          const int (&hi)[kQ], const bool (&ok)[kQ],
+                                          bool uni, bool (&stiff)[kQ],
+                                          float (&v)[kQ][WM]) {
+  int w[kQ];
 #pragma unroll
-  for (int r = 0; r < WM; ++r) v[r] = st.P[r][lane];  // r >= w: ignored
-  float dne = 0.0f;
-  int nlo = lo, nhi = hi;
-  bool stiff = false;
-  if constexpr (WM >= 2) {
-    const FieldF32 f = field_f32(Ec);
-    const bool live = w >= 2 && !f.zero && !a.zero_dt;
-    float lam[WM];
-    float y0[WM];
-    bool need_precise = false;
+  for (int j = 0; j < kQ; ++j) w[j] = ok[j] ? hi[j] - lo[j] + 1 : 0;
 #pragma unroll
-    for (int r = 0; r < WM - 1; ++r) {
-      const float4 h = tab.hi[min(lo + r, ION_MAX_Z)];
-      const float q = h.z * f.rE;
-      y0[r] = fmaf(-h.y, f.lg, h.x) - q;
-      const bool on = live && r < w - 1 && q <= (float)kCutoffLog2;
-      lam[r] = on ? ex2_approx(y0[r]) : 0.0f;
-      need_precise |= on && y0[r] >= -12.0f;
-    }
-    lam[WM - 1] = 0.0f;
-    if (need_precise) {
+  for (int r = 0; r < WM; ++r) {
+    const float4 p = st.P[r][lane];
+    v[0][r] = p.x;
+    v[1][r] = p.y;
+    v[2][r] = p.z;
+    v[3][r] = p.w;
+  }
+  float lam[kQ][WM];
+  int Rl = 0;
 #pragma unroll
-      for (int r = 0; r < WM - 1; ++r)
-        if (lam[r] != 0.0f && y0[r] >= -12.0f) lam[r] = rate_dt_f32(tab, lo + r, f);
-    }
-    float lmax = 0.0f;
+  for (int j = 0; j < kQ; ++j) {
+    stiff[j] = false;
 #pragma unroll
-    for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[r]);
-    stiff = lmax > kLamEasy;
-    // terms of exp(dt A) v: R = number of thresholds below 2 lmax (<= 4)
-    const float x = stiff ? 0.0f : 2.0f * lmax;
-    int R = 0;
-#pragma unroll
-    for (int i = 0; i < kEasyTerms; ++i) R += x > kThrF32[i] ? 1 : 0;
-    const int Rw = __reduce_max_sync(kFull, R);
-    if (!stiff && w >= 2) {
-      float t[WM], inc[WM];
-#pragma unroll
-      for (int i = 0; i < WM; ++i) {
-        t[i] = i < w ? v[i] : 0.0f;
-        inc[i] = 0.0f;
-      }
-#pragma unroll
-      for (int k = 1; k <= kEasyTerms; ++k) {
-        if (k > Rw) break;
-        const float rk = 1.0f / k;
-#pragma unroll
-        for (int i = WM - 1; i >= 0; --i) {
-          const float gain = i > 0 ? lam[i - 1] * t[i - 1] : 0.0f;
-          t[i] = (gain - lam[i] * t[i]) * rk;
-          inc[i] += t[i];
-        }
-      }
-      float cum = 0.0f;
+    for (int r = 0; r < WM; ++r) lam[j][r] = 0.0f;
+    if constexpr (WM >= 2) {
+      const FieldF32 f = field_f32(Ev[j]);
+      const bool live = w[j] >= 2 && !f.zero && !a.zero_dt;
+      const int base = ok[j] ? lo[j] : 0;
+      float y0[WM];
+      bool need_precise = false;
 #pragma unroll
       for (int r = 0; r < WM - 1; ++r) {
-        if (r < w - 1) {
-          cum -= inc[r];  // population that left states <= r
-          dne += cum;
-        }
+        const float4 h = tab.hi[min(base + r, ION_MAX_Z)];
+        const float q = h.z * f.rE;
+        y0[r] = fmaf(-h.y, f.lg, h.x) - q;
+        const bool on = live && r < w[j] - 1 && q <= (float)kCutoffLog2;
+        lam[j][r] = on ? ex2_approx(y0[r]) : 0.0f;
+        need_precise |= on && y0[r] >= -12.0f;
       }
+      if (need_precise) {
 #pragma unroll
-      for (int r = 0; r < WM; ++r) v[r] += inc[r];
-      if ((a.flags & ION_NO_WINDOW_UPDATE) == 0 && v[0] < (float)a.eps && hi < a.Z)
-        slide_window<float, WM>(v, w, a.Z, (float)a.eps, nlo, nhi);
-      float* p = static_cast<float*>(a.N) + (int64_t)lo * a.ld + c;
-#pragma unroll
-      for (int r = 0; r < WM; ++r) {
-        if (r < w) __stcs(p, v[r]);
-        p += a.ld;
+        for (int r = 0; r < WM - 1; ++r)
+          if (lam[j][r] != 0.0f && y0[r] >= -12.0f)
+            lam[j][r] = rate_dt_f32(tab, base + r, f);
       }
+      float lmax = 0.0f;
+#pragma unroll
+      for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
+      stiff[j] = lmax > kLamEasy;
+      const float x = stiff[j] ? 0.0f : 2.0f * lmax;
+      int R = 0;
+#pragma unroll
+      for (int i = 0; i < kEasyTerms; ++i) R += x > kThrF32[i] ? 1 : 0;
+      Rl = max(Rl, R);
     }
   }
-  if (stiff || !ok) return stiff;
-  const float* __restrict__ G = static_cast<const float*>(a.n_gas);
-  __stcs(static_cast<float*>(a.dne) + c, G ? dne * G[c] : dne);
-  if (nlo != lo) {
-    a.lo[c] = (uint8_t)nlo;
-    a.hi[c] = (uint8_t)nhi;
+  if constexpr (WM < 2) return;
+  const int Rw = __reduce_max_sync(kFull, Rl);
+  float dne[kQ];
+  int nlo[kQ], nhi[kQ];
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    dne[j] = 0.0f;
+    nlo[j] = lo[j];
+    nhi[j] = hi[j];
+    if (stiff[j] || w[j] < 2) continue;
+    float t[WM], inc[WM];
+#pragma unroll
+    for (int i = 0; i < WM; ++i) {
+      t[i] = i < w[j] ? v[j][i] : 0.0f;
+      inc[i] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 1; k <= kEasyTerms; ++k) {
+      if (k > Rw) break;
+      const float rk = 1.0f / k;
+#pragma unroll
+      for (int i = WM - 1; i >= 0; --i) {
+        const float gain = i > 0 ? lam[j][i - 1] * t[i - 1] : 0.0f;
+        t[i] = (gain - lam[j][i] * t[i]) * rk;
+        inc[i] += t[i];
+      }
+    }
+    float cum = 0.0f;
+#pragma unroll
+    for (int r = 0; r < WM - 1; ++r) {
+      if (r < w[j] - 1) {
+        cum -= inc[r];  // population that left states <= r
+        dne[j] += cum;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < WM; ++r) v[j][r] += inc[r];
+    if ((a.flags & ION_NO_WINDOW_UPDATE) == 0 && v[j][0] < (float)a.eps && hi[j] < a.Z)
+      slide_window<float, WM>(v[j], w[j], a.Z, (float)a.eps, nlo[j], nhi[j]);
   }
-  return false;
+  // stores
+  const float* __restrict__ G = static_cast<const float*>(a.n_gas);
+  if (G) {
+#pragma unroll
+    for (int j = 0; j < kQ; ++j)
+      if (ok[j] && !stiff[j]) dne[j] *= G[c0 + j];
+  }
+  const bool whole = uni && !stiff[0] && !stiff[1] && !stiff[2] && !stiff[3];
+  float* __restrict__ N = static_cast<float*>(a.N);
+  float* __restrict__ D = static_cast<float*>(a.dne);
+  if (whole && a.vec) {
+    float* p = N + (int64_t)lo[0] * a.ld + c0;
+#pragma unroll
+    for (int r = 0; r < WM; ++r) {
+      if (r < w[0])
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0][r], v[1][r], v[2][r], v[3][r]));
+      p += a.ld;
+    }
+    __stcs(reinterpret_cast<float4*>(D + c0), make_float4(dne[0], dne[1], dne[2], dne[3]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+      if (!ok[j] || stiff[j]) continue;
+      float* p = N + (int64_t)lo[j] * a.ld + c0 + j;
+#pragma unroll
+      for (int r = 0; r < WM; ++r) {
+        if (r < w[j]) __stcs(p, v[j][r]);
+        p += a.ld;
+      }
+      __stcs(D + c0 + j, dne[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    if (ok[j] && !stiff[j] && nlo[j] != lo[j]) {
+      a.lo[c0 + j] = (uint8_t)nlo[j];
+      a.hi[c0 + j] = (uint8_t)nhi[j];
+    }
+  }
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 8)
+// Width-1 quads: nothing moves; only dne = 0 is written.
+__device__ __forceinline__ void trivial_quad(const StepArgs& a, int c0,
+                                             const bool (&ok)[kQ]) {
+  float* D = static_cast<float*>(a.dne);
+#pragma unroll
+  for (int j = 0; j < kQ; ++j)
+    if (ok[j]) __stcs(D + c0 + j, 0.0f);
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 4)
     ion_step_f32_kernel(const __grid_constant__ StepArgs a) {
+  constexpr int kStagesQ = 3;
   __shared__ StagedF32 tab;
-  __shared__ ChunkStage ring[kWarps][kStages];
+  __shared__ QuadStage ring[kWarps][kStagesQ];
   stage_f32(a.tab, a.log2dt, &tab);
   {
-    // plane slots past a cell's window are read (and ignored) by the easy
-    // path; keep them finite
+    // plane slots past a cell's window are read (and ignored); keep them
+    // finite
     float* z = reinterpret_cast<float*>(&ring[0][0]);
     for (int i = threadIdx.x; i < (int)(sizeof(ring) / sizeof(float)); i += blockDim.x)
       z[i] = 0.0f;
@@ -331,39 +401,62 @@ __global__ void __launch_bounds__(kWarps * 32, 8)
 
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  ChunkStage* S = ring[wib];
+  QuadStage* S = ring[wib];
   const int gw = blockIdx.x * kWarps + wib;
   const int TW = gridDim.x * kWarps;
-  const int nfull = a.ncells >> 5;
+  const int nfull = a.ncells / kChunk;
   const int K = gw < nfull ? (nfull - 1 - gw) / TW + 1 : 0;
   const float* __restrict__ E = static_cast<const float*>(a.E);
   const float* __restrict__ N = static_cast<const float*>(a.N);
   const int64_t ld = a.ld;
 
-  // |E|, k_lo, k_hi of the warp's chunk k into its stage (one commit group).
+  // |E|, k_lo, k_hi of the lane's quad of chunk k (one commit group)
   auto issue_front = [&](int k) {
     if (k < K) {
-      const int c0 = (gw + k * TW) << 5;
-      ChunkStage& st = S[k % kStages];
-      cp_async4(&st.E[lane], E + c0 + lane);
-      if (lane < 8)
-        cp_async4(&st.lo[4 * lane], a.lo + c0 + 4 * lane);
-      else if (lane < 16)
-        cp_async4(&st.hi[4 * (lane - 8)], a.hi + c0 + 4 * (lane - 8));
+      const int c0 = (gw + k * TW) * kChunk + kQ * lane;
+      QuadStage& st = S[k % kStagesQ];
+      if (a.vec) {
+        cp_async16(&st.E[lane], E + c0);
+      } else {
+        float* e = reinterpret_cast<float*>(&st.E[lane]);
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) cp_async4(e + j, E + c0 + j);
+      }
+      cp_async4(&st.lo[lane], a.lo + c0);
+      cp_async4(&st.hi[lane], a.hi + c0);
     }
     cp_async_commit();
   };
-  // the window planes of the lane's cell of chunk k (one commit group).
+  // the window planes of the lane's quad of chunk k (one commit group)
   auto issue_planes = [&](int k) {
     if (k < K) {
-      const int c = ((gw + k * TW) << 5) + lane;
-      ChunkStage& st = S[k % kStages];
-      const int lo = st.lo[lane], hi = st.hi[lane];
-      const int w = window_ok(lo, hi, a.Z) ? hi - lo + 1 : 0;
-      const float* p = N + (int64_t)lo * ld + c;
-      for (int r = 0; r < w; ++r) {
-        cp_async4(&st.P[r][lane], p);
-        p += ld;
+      const int c0 = (gw + k * TW) * kChunk + kQ * lane;
+      QuadStage& st = S[k % kStagesQ];
+      const uint32_t l4 = st.lo[lane], h4 = st.hi[lane];
+      int lo[kQ], w[kQ];
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) {
+        lo[j] = (l4 >> (8 * j)) & 0xff;
+        const int hj = (h4 >> (8 * j)) & 0xff;
+        w[j] = window_ok(lo[j], hj, a.Z) ? hj - lo[j] + 1 : 0;
+      }
+      if (a.vec && l4 == ((l4 & 0xff) * 0x01010101u) && h4 == ((h4 & 0xff) * 0x01010101u) &&
+          w[0] > 0) {
+        const float* p = N + (int64_t)lo[0] * ld + c0;
+        for (int r = 0; r < w[0]; ++r) {
+          cp_async16(&st.P[r][lane], p);
+          p += ld;
+        }
+      } else {
+        float* P0 = reinterpret_cast<float*>(&st.P[0][lane]);
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+          const float* p = N + (int64_t)lo[j] * ld + c0 + j;
+          for (int r = 0; r < w[j]; ++r) {
+            cp_async4(P0 + r * 128 + j, p);
+            p += ld;
+          }
+        }
       }
     }
     cp_async_commit();
@@ -382,49 +475,78 @@ __global__ void __launch_bounds__(kWarps * 32, 8)
     cp_async_wait<2>();  // planes(k): pending are front(k+2), planes(k+1)
     __syncwarp();
 
-    const ChunkStage& st = S[k % kStages];
-    const int c = ((gw + k * TW) << 5) + lane;
-    const float Ec = st.E[lane];
-    const int lo = st.lo[lane], hi = st.hi[lane];
-    const bool ok = window_ok(lo, hi, a.Z);
-    if (!ok) atomicAdd(&a.hdr[kHdrInvalid], 1u);
-    const int WMw = __reduce_max_sync(kFull, ok ? hi - lo + 1 : 0);
-    bool stiff;
-    if (WMw <= 1)
-      stiff = easy_cell<1>(a, tab, st, lane, c, Ec, lo, hi, ok);
-    else if (WMw == 2)
-      stiff = easy_cell<2>(a, tab, st, lane, c, Ec, lo, hi, ok);
-    else if (WMw <= 4)
-      stiff = easy_cell<4>(a, tab, st, lane, c, Ec, lo, hi, ok);
-    else
-      stiff = easy_cell<6>(a, tab, st, lane, c, Ec, lo, hi, ok);
-    append_record(a, stiff, c, Ec, lo, hi, &st.P[0][lane], 32);
+    const QuadStage& st = S[k % kStagesQ];
+    const int c0 = (gw + k * TW) * kChunk + kQ * lane;
+    const float4 e4 = st.E[lane];
+    const float Ev[kQ] = {e4.x, e4.y, e4.z, e4.w};
+    const uint32_t l4 = st.lo[lane], h4 = st.hi[lane];
+    int lo[kQ], hi[kQ], wl = 0, nbad = 0;
+    bool ok[kQ];
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+      lo[j] = (l4 >> (8 * j)) & 0xff;
+      hi[j] = (h4 >> (8 * j)) & 0xff;
+      ok[j] = window_ok(lo[j], hi[j], a.Z);
+      nbad += ok[j] ? 0 : 1;
+      wl = ok[j] ? max(wl, hi[j] - lo[j] + 1) : wl;
+    }
+    if (nbad) atomicAdd(&a.hdr[kHdrInvalid], (unsigned)nbad);
+    const bool uni = nbad == 0 && l4 == ((l4 & 0xff) * 0x01010101u) &&
+                     h4 == ((h4 & 0xff) * 0x01010101u);
+    const int WMw = __reduce_max_sync(kFull, wl);
+    bool stiff[kQ] = {false, false, false, false};
+    if (WMw <= 1) {
+      trivial_quad(a, c0, ok);
+    } else if (WMw == 2) {
+      float v[kQ][2];
+      easy_quad<2>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, v);
+    } else if (WMw <= 4) {
+      float v[kQ][4];
+      easy_quad<4>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, v);
+    } else {
+      float v[kQ][6];
+      easy_quad<6>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, v);
+    }
+    // stiff cells: their inputs (as loaded) go to the record queue
+    if (__ballot_sync(kFull, stiff[0] || stiff[1] || stiff[2] || stiff[3])) {
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) {
+        float vin[ION_MAX_WINDOW];
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = f4get(st.P[r][lane], j);
+        append_record(a, stiff[j], c0 + j, Ev[j], lo[j], hi[j], vin);
+      }
+    }
     __syncwarp();
   }
   cp_async_wait<0>();
 
-  // the last, partial chunk (ncells % 32 cells): every valid cell becomes a
+  // the last, partial chunk (ncells % 128 cells): every valid cell becomes a
   // record for the stiff kernel, which runs the full path
-  const int tail = a.ncells & 31;
-  if (tail && gw == TW - 1) {
-    const int c = (nfull << 5) + lane;
-    bool take = false;
-    float Ec = 0.0f, v[ION_MAX_WINDOW];
-    int lo = 0, hi = 0;
-    if (lane < tail) {
-      Ec = E[c];
-      lo = a.lo[c];
-      hi = a.hi[c];
-      take = window_ok(lo, hi, a.Z);
-      if (!take) atomicAdd(&a.hdr[kHdrInvalid], 1u);
-      const float* p = N + (int64_t)lo * ld + c;
+  const int tail0 = nfull * kChunk;
+  if (tail0 < a.ncells && gw == TW - 1) {
+    for (int cb = tail0; cb < a.ncells; cb += 32) {
+      const int c = cb + lane;
+      bool take = false;
+      float Ec = 0.0f, v[ION_MAX_WINDOW];
+      int lo = 0, hi = 0;
 #pragma unroll
-      for (int r = 0; r < ION_MAX_WINDOW; ++r) {
-        v[r] = (take && r < hi - lo + 1) ? p[0] : 0.0f;
-        p += ld;
+      for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = 0.0f;
+      if (c < a.ncells) {
+        Ec = E[c];
+        lo = a.lo[c];
+        hi = a.hi[c];
+        take = window_ok(lo, hi, a.Z);
+        if (!take) atomicAdd(&a.hdr[kHdrInvalid], 1u);
+        const float* p = N + (int64_t)lo * ld + c;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+          if (take && r < hi - lo + 1) v[r] = p[0];
+          p += ld;
+        }
       }
+      append_record(a, take, c, Ec, lo, hi, v);
     }
-    append_record(a, take, c, Ec, lo, hi, v, 1);
   }
 }
 
@@ -612,7 +734,7 @@ cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   if (a.ncells == 0) return cudaSuccess;
-  const int64_t chunks = ((int64_t)a.ncells + 31) / 32;
+  const int64_t chunks = ((int64_t)a.ncells + kChunk - 1) / kChunk;
   const int64_t need = (chunks + kWarps - 1) / kWarps;
   const int64_t cap = (int64_t)resident_blocks_f32() * num_sms;
   const int blocks = (int)(need < cap ? need : cap);
