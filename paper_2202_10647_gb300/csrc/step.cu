@@ -234,9 +234,9 @@ __device__ __forceinline__ float f4get(const float4& x, int j) {
 // lane of the warp calls this.  Cells whose rates all have W dt <= kLamEasy
 // are finished; stiff[j] marks the others, which are left untouched.
 // Written for lanes that mostly agree: every window rate takes the plain
-// FP32 exponent, the float-float refinement runs only for rates above 2^-12,
-// and the Taylor series runs the warp's largest term count (extra terms only
-// add accuracy).
+// FP32 exponent (the stiff path recomputes its rates in float-float), and
+// the Taylor series runs the warp's largest term count (extra terms only add
+// accuracy).
 template <int WM>
 __device__ __forceinline__ void easy_quad(const StepArgs& a, const StagedF32& tab,
                                           const QuadStage& st, int lane, int c0,
@@ -263,25 +263,20 @@ __device__ __forceinline__ void easy_quad(const StepArgs& a, const StagedF32& ta
 #pragma unroll
     for (int r = 0; r < WM; ++r) lam[j][r] = 0.0f;
     if constexpr (WM >= 2) {
+      // Plain FP32 exponent y = (a_hi + a_lo) - b log2|E| - C/|E|: its
+      // error is below ~6e-5 in log2 units even for terms of 10^3, i.e. a
+      // relative error of W dt below 4e-5, which moves populations by at most
+      // 0.025 * 4e-5 = 1e-6 in the cells this path finishes (W dt <= 0.025).
       const FieldF32 f = field_f32(Ev[j]);
       const bool live = w[j] >= 2 && !f.zero && !a.zero_dt;
       const int base = ok[j] ? lo[j] : 0;
-      float y0[WM];
-      bool need_precise = false;
 #pragma unroll
       for (int r = 0; r < WM - 1; ++r) {
         const float4 h = tab.hi[min(base + r, ION_MAX_Z)];
         const float q = h.z * f.rE;
-        y0[r] = fmaf(-h.y, f.lg, h.x) - q;
+        const float y = (fmaf(-h.y, f.lg, h.x) - q) + h.w;
         const bool on = live && r < w[j] - 1 && q <= (float)kCutoffLog2;
-        lam[j][r] = on ? ex2_approx(y0[r]) : 0.0f;
-        need_precise |= on && y0[r] >= -12.0f;
-      }
-      if (need_precise) {
-#pragma unroll
-        for (int r = 0; r < WM - 1; ++r)
-          if (lam[j][r] != 0.0f && y0[r] >= -12.0f)
-            lam[j][r] = rate_dt_f32(tab, base + r, f);
+        lam[j][r] = on ? ex2_approx(fminf(y, 99.0f)) : 0.0f;
       }
       float lmax = 0.0f;
 #pragma unroll
@@ -410,11 +405,12 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
   const float* __restrict__ N = static_cast<const float*>(a.N);
   const int64_t ld = a.ld;
 
-  // |E|, k_lo, k_hi of the lane's quad of chunk k (one commit group)
-  auto issue_front = [&](int k) {
+  // |E|, k_lo, k_hi of the lane's quad of chunk k into stage `sg` (one
+  // commit group)
+  auto issue_front = [&](int k, int sg) {
     if (k < K) {
       const int c0 = (gw + k * TW) * kChunk + kQ * lane;
-      QuadStage& st = S[k % kStagesQ];
+      QuadStage& st = S[sg];
       if (a.vec) {
         cp_async16(&st.E[lane], E + c0);
       } else {
@@ -427,32 +423,32 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     }
     cp_async_commit();
   };
-  // the window planes of the lane's quad of chunk k (one commit group)
-  auto issue_planes = [&](int k) {
+  // the window planes of the lane's quad of chunk k in stage `sg` (one
+  // commit group)
+  auto issue_planes = [&](int k, int sg) {
     if (k < K) {
       const int c0 = (gw + k * TW) * kChunk + kQ * lane;
-      QuadStage& st = S[k % kStagesQ];
+      QuadStage& st = S[sg];
       const uint32_t l4 = st.lo[lane], h4 = st.hi[lane];
-      int lo[kQ], w[kQ];
-#pragma unroll
-      for (int j = 0; j < kQ; ++j) {
-        lo[j] = (l4 >> (8 * j)) & 0xff;
-        const int hj = (h4 >> (8 * j)) & 0xff;
-        w[j] = window_ok(lo[j], hj, a.Z) ? hj - lo[j] + 1 : 0;
-      }
-      if (a.vec && l4 == ((l4 & 0xff) * 0x01010101u) && h4 == ((h4 & 0xff) * 0x01010101u) &&
-          w[0] > 0) {
-        const float* p = N + (int64_t)lo[0] * ld + c0;
-        for (int r = 0; r < w[0]; ++r) {
-          cp_async16(&st.P[r][lane], p);
+      const int lo0 = l4 & 0xff, hi0 = h4 & 0xff;
+      if (a.vec && l4 == lo0 * 0x01010101u && h4 == hi0 * 0x01010101u) {
+        // the quad shares its window: one 16-byte copy per plane
+        const int w = window_ok(lo0, hi0, a.Z) ? hi0 - lo0 + 1 : 0;
+        const float* p = N + (int64_t)lo0 * ld + c0;
+        float4* d = &st.P[0][lane];
+        for (int r = 0; r < w; ++r) {
+          cp_async16(d, p);
           p += ld;
+          d += 32;
         }
       } else {
         float* P0 = reinterpret_cast<float*>(&st.P[0][lane]);
 #pragma unroll
         for (int j = 0; j < kQ; ++j) {
-          const float* p = N + (int64_t)lo[j] * ld + c0 + j;
-          for (int r = 0; r < w[j]; ++r) {
+          const int lj = (l4 >> (8 * j)) & 0xff, hj = (h4 >> (8 * j)) & 0xff;
+          const int w = window_ok(lj, hj, a.Z) ? hj - lj + 1 : 0;
+          const float* p = N + (int64_t)lj * ld + c0 + j;
+          for (int r = 0; r < w; ++r) {
             cp_async4(P0 + r * 128 + j, p);
             p += ld;
           }
@@ -462,37 +458,55 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     cp_async_commit();
   };
 
-  issue_front(0);
-  issue_front(1);
+  // stages: chunk k lives in s0, k+1 in s1, k+2 in s2 (a rotation of 0,1,2)
+  int s0 = 0, s1 = 1, s2 = 2;
+  issue_front(0, s0);
+  issue_front(1, s1);
   cp_async_wait<1>();  // front(0)
   __syncwarp();
-  issue_planes(0);
+  issue_planes(0, s0);
   for (int k = 0; k < K; ++k) {
-    issue_front(k + 2);
+    issue_front(k + 2, s2);
     cp_async_wait<2>();  // front(k+1): pending are planes(k), front(k+2)
     __syncwarp();
-    issue_planes(k + 1);
+    issue_planes(k + 1, s1);
     cp_async_wait<2>();  // planes(k): pending are front(k+2), planes(k+1)
     __syncwarp();
 
-    const QuadStage& st = S[k % kStagesQ];
+    const QuadStage& st = S[s0];
     const int c0 = (gw + k * TW) * kChunk + kQ * lane;
     const float4 e4 = st.E[lane];
     const float Ev[kQ] = {e4.x, e4.y, e4.z, e4.w};
     const uint32_t l4 = st.lo[lane], h4 = st.hi[lane];
-    int lo[kQ], hi[kQ], wl = 0, nbad = 0;
+    int lo[kQ], hi[kQ], wl = 0;
     bool ok[kQ];
+    const bool same = l4 == (l4 & 0xff) * 0x01010101u && h4 == (h4 & 0xff) * 0x01010101u;
+    bool uni;
+    if (same) {
+      const int l0 = l4 & 0xff, h0 = h4 & 0xff;
+      const bool o = window_ok(l0, h0, a.Z);
 #pragma unroll
-    for (int j = 0; j < kQ; ++j) {
-      lo[j] = (l4 >> (8 * j)) & 0xff;
-      hi[j] = (h4 >> (8 * j)) & 0xff;
-      ok[j] = window_ok(lo[j], hi[j], a.Z);
-      nbad += ok[j] ? 0 : 1;
-      wl = ok[j] ? max(wl, hi[j] - lo[j] + 1) : wl;
+      for (int j = 0; j < kQ; ++j) {
+        lo[j] = l0;
+        hi[j] = h0;
+        ok[j] = o;
+      }
+      wl = o ? h0 - l0 + 1 : 0;
+      if (!o) atomicAdd(&a.hdr[kHdrInvalid], (unsigned)kQ);
+      uni = o;
+    } else {
+      int nbad = 0;
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) {
+        lo[j] = (l4 >> (8 * j)) & 0xff;
+        hi[j] = (h4 >> (8 * j)) & 0xff;
+        ok[j] = window_ok(lo[j], hi[j], a.Z);
+        nbad += ok[j] ? 0 : 1;
+        wl = ok[j] ? max(wl, hi[j] - lo[j] + 1) : wl;
+      }
+      if (nbad) atomicAdd(&a.hdr[kHdrInvalid], (unsigned)nbad);
+      uni = false;
     }
-    if (nbad) atomicAdd(&a.hdr[kHdrInvalid], (unsigned)nbad);
-    const bool uni = nbad == 0 && l4 == ((l4 & 0xff) * 0x01010101u) &&
-                     h4 == ((h4 & 0xff) * 0x01010101u);
     const int WMw = __reduce_max_sync(kFull, wl);
     bool stiff[kQ] = {false, false, false, false};
     if (WMw <= 1) {
@@ -518,6 +532,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
       }
     }
     __syncwarp();
+    const int t = s0;
+    s0 = s1;
+    s1 = s2;
+    s2 = t;
   }
   cp_async_wait<0>();
 
