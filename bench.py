@@ -380,19 +380,18 @@ def main():
                    "form": "FP32 + FP64 coefficients for |W_i-W_j| < 1e-3 max(W_i,W_j)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "ion_step (ion_step_f32_kernel + _medium + _stiff + ion_step_fb_kernel)",
+                     "kernel": "ion_step (ion_step_f32_kernel + ion_step_f32_hard_kernel + ion_step_fb_kernel)",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": main_ms},
         "forms": {
             "fp32_fp64fallback": {"value": value, "ms_per_step": ms_per_step,
                                   "fp64_coefficient_cells": fb_cells,
-                                  "taylor_long_path_cells": stiff[0],
-                                  "bateman_cells": stiff[1]},
+                                  "second_kernel_cells": stiff},
             "fp64_plain": {"value": n / (ms64 * 1e-3), "ms_per_step": ms64,
                            "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9},
         },
         "accuracy": acc,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -160,9 +160,8 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *          the step the header holds uint32 counters: word 0 the cells
  *          whose coefficients were computed in FP64, word 1 the cells left
  *          untouched because their window was invalid (lo > hi, hi > Z or
- *          w > ION_MAX_WINDOW), words 2 and 3 the cells that had a rate
- *          with W dt > 0.025 and were finished by the second kernels, in
- *          the Taylor form (every W dt <= 1) and in the Bateman form.
+ *          w > ION_MAX_WINDOW), word 2 the cells that had a rate with
+ *          W dt > 0.025 (finished on the long path).
  * Alignment: E, N, dne, n_gas aligned to their element size; with ION_F32
  * k_lo and k_hi 4-byte aligned (they are copied four cells at a time).
  * Calls that share a workspace must not overlap on the device.

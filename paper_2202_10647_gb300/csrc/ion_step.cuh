@@ -12,9 +12,8 @@ namespace ion {
 // Workspace header (uint32 words at the start of the workspace).
 constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
 constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
-constexpr int kHdrMedium = 2;    // records finished in the Taylor form (W dt <= 1)
-constexpr int kHdrStiff = 3;     // records finished in the Bateman form
-constexpr int kHdrWords = 4;
+constexpr int kHdrStiff = 2;     // stiff-cell records written by the streaming kernel
+constexpr int kHdrWords = 3;
 constexpr size_t kHdrBytes = 256;
 
 struct StepArgs {

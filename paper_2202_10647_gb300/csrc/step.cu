@@ -203,33 +203,26 @@ struct QuadStage {
   float4 P[ION_MAX_WINDOW][32];   // P[r][lane].j = N[lo_j + r] of cell j
 };
 
-// Appends the record of a cell for a second kernel (one atomic per warp per
-// queue).  Every lane of the warp calls this; `take` lanes pass their cell's
-// inputs.  Medium cells (every W dt <= 1, Taylor form) fill the record
-// arrays from the front, stiff cells (Bateman form) from the back.
-__device__ __forceinline__ void append_record(const StepArgs& a, bool take,
-                                              bool medium, int c, float Ec, int lo,
-                                              int hi, const float* v) {
+// Appends the record of a stiff cell (one atomic per warp).  Every lane of
+// the warp calls this; `take` lanes pass their cell's inputs.
+__device__ __forceinline__ void append_record(const StepArgs& a, bool take, int c,
+                                              float Ec, int lo, int hi,
+                                              const float* v) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(&a.hdr[kHdrStiff], (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, 0);
+  if (take) {
+    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
+    a.rec_c[i] = (uint32_t)c;
+    a.rec_E[i] = Ec;
+    a.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
+    const int w = hi - lo + 1;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const bool tq = take && (medium == (q == 0));
-    const unsigned m = __ballot_sync(kFull, tq);
-    if (!m) continue;
-    const int lane = threadIdx.x & 31;
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&a.hdr[q == 0 ? kHdrMedium : kHdrStiff], (unsigned)__popc(m));
-    base = __shfl_sync(kFull, base, 0);
-    if (tq) {
-      const unsigned k = base + __popc(m & ((1u << lane) - 1u));
-      const int64_t i = q == 0 ? (int64_t)k : a.rec_cap - 1 - (int64_t)k;
-      a.rec_c[i] = (uint32_t)c;
-      a.rec_E[i] = Ec;
-      a.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
-      const int w = hi - lo + 1;
-#pragma unroll
-      for (int r = 0; r < ION_MAX_WINDOW; ++r)
-        if (r < w) a.rec_V[(int64_t)r * a.rec_cap + i] = v[r];
-    }
+    for (int r = 0; r < ION_MAX_WINDOW; ++r)
+      if (r < w) a.rec_V[(int64_t)r * a.rec_cap + i] = v[r];
   }
 }
 
@@ -250,7 +243,7 @@ __device__ __forceinline__ void easy_quad(const StepArgs& a, const StagedF32& ta
                                           const float (&Ev)[kQ], const int (&lo)[kQ],
                                           const int (&hi)[kQ], const bool (&ok)[kQ],
                                           bool uni, bool (&stiff)[kQ],
-                                          bool (&medium)[kQ], float (&v)[kQ][WM]) {
+                                          float (&v)[kQ][WM]) {
   int w[kQ];
 #pragma unroll
   for (int j = 0; j < kQ; ++j) w[j] = ok[j] ? hi[j] - lo[j] + 1 : 0;
@@ -267,7 +260,6 @@ __device__ __forceinline__ void easy_quad(const StepArgs& a, const StagedF32& ta
 #pragma unroll
   for (int j = 0; j < kQ; ++j) {
     stiff[j] = false;
-    medium[j] = true;
 #pragma unroll
     for (int r = 0; r < WM; ++r) lam[j][r] = 0.0f;
     if constexpr (WM >= 2) {
@@ -290,7 +282,6 @@ __device__ __forceinline__ void easy_quad(const StepArgs& a, const StagedF32& ta
 #pragma unroll
       for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
       stiff[j] = lmax > kLamEasy;
-      medium[j] = lmax <= DDParams<float>::prop_max;
       const float x = stiff[j] ? 0.0f : 2.0f * lmax;
       int R = 0;
 #pragma unroll
@@ -518,28 +509,26 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
     }
     const int WMw = __reduce_max_sync(kFull, wl);
     bool stiff[kQ] = {false, false, false, false};
-    bool medium[kQ] = {true, true, true, true};
     if (WMw <= 1) {
       trivial_quad(a, c0, ok);
     } else if (WMw == 2) {
       float v[kQ][2];
-      easy_quad<2>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, medium, v);
+      easy_quad<2>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, v);
     } else if (WMw <= 4) {
       float v[kQ][4];
-      easy_quad<4>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, medium, v);
+      easy_quad<4>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, v);
     } else {
       float v[kQ][6];
-      easy_quad<6>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, medium, v);
+      easy_quad<6>(a, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, v);
     }
-    // cells left for the second kernels: their inputs (as loaded) become
-    // records
+    // stiff cells: their inputs (as loaded) go to the record queue
     if (__ballot_sync(kFull, stiff[0] || stiff[1] || stiff[2] || stiff[3])) {
 #pragma unroll
       for (int j = 0; j < kQ; ++j) {
         float vin[ION_MAX_WINDOW];
 #pragma unroll
         for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = f4get(st.P[r][lane], j);
-        append_record(a, stiff[j], medium[j], c0 + j, Ev[j], lo[j], hi[j], vin);
+        append_record(a, stiff[j], c0 + j, Ev[j], lo[j], hi[j], vin);
       }
     }
     __syncwarp();
@@ -574,115 +563,15 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
           p += ld;
         }
       }
-      append_record(a, take, false, c, Ec, lo, hi, v);
+      append_record(a, take, c, Ec, lo, hi, v);
     }
   }
 }
 
-// Medium records (every W dt <= 1): float-float rates and the Taylor form,
-// one record per lane with warp-uniform code (the warp's widest window sets
-// the loops; the warp's largest term count is run by every lane).
-template <int WM>
-__device__ __forceinline__ void medium_cell(const StepArgs& a, const StagedF32& tab,
-                                            int64_t i, bool in) {
-  int c = 0, lo = 0, hi = 0, w = 0;
-  float Ec = 0.0f, v[WM];
-  if (in) {
-    c = (int)__ldcs(a.rec_c + i);
-    Ec = __ldcs(a.rec_E + i);
-    const unsigned lh = __ldcs(a.rec_lohi + i);
-    lo = lh & 0xff;
-    hi = lh >> 8;
-    w = hi - lo + 1;
-  }
-#pragma unroll
-  for (int r = 0; r < WM; ++r)
-    v[r] = (r < w) ? __ldcs(a.rec_V + (int64_t)r * a.rec_cap + i) : 0.0f;
-  const FieldF32 f = field_f32(Ec);
-  float lam[WM], lmax = 0.0f;
-#pragma unroll
-  for (int r = 0; r < WM; ++r) {
-    lam[r] = (r < w - 1 && !a.zero_dt) ? rate_dt_f32(tab, lo + r, f) : 0.0f;
-    lmax = fmaxf(lmax, lam[r]);
-  }
-  using P = DDParams<float>;
-  const int R = __reduce_max_sync(kFull, P::terms(2.0f * lmax, P::PMAX));
-  float t[WM], inc[WM];
-#pragma unroll
-  for (int r = 0; r < WM; ++r) {
-    t[r] = v[r];
-    inc[r] = 0.0f;
-  }
-#pragma unroll
-  for (int k = 1; k <= P::PMAX; ++k) {
-    if (k > R) break;
-    const float rk = 1.0f / k;
-#pragma unroll
-    for (int r = WM - 1; r >= 0; --r) {
-      const float gain = r > 0 ? lam[r - 1] * t[r - 1] : 0.0f;
-      t[r] = (gain - lam[r] * t[r]) * rk;
-      inc[r] += t[r];
-    }
-  }
-  if (!in) return;
-  float cum = 0.0f, dne = 0.0f;
-#pragma unroll
-  for (int r = 0; r < WM - 1; ++r) {
-    if (r < w - 1) {
-      cum -= inc[r];
-      dne += cum;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < WM; ++r) v[r] += inc[r];
-  int nlo = lo, nhi = hi;
-  if ((a.flags & ION_NO_WINDOW_UPDATE) == 0)
-    slide_window<float, WM>(v, w, a.Z, (float)a.eps, nlo, nhi);
-  float* p = static_cast<float*>(a.N) + (int64_t)lo * a.ld + c;
-#pragma unroll
-  for (int r = 0; r < WM; ++r) {
-    if (r < w) __stcs(p, v[r]);
-    p += a.ld;
-  }
-  const float* __restrict__ G = static_cast<const float*>(a.n_gas);
-  __stcs(static_cast<float*>(a.dne) + c, G ? dne * G[c] : dne);
-  if (nlo != lo) {
-    a.lo[c] = (uint8_t)nlo;
-    a.hi[c] = (uint8_t)nhi;
-  }
-}
-
-__global__ void __launch_bounds__(256)
-    ion_step_f32_medium_kernel(const __grid_constant__ StepArgs a) {
-  __shared__ StagedF32 tab;
-  stage_f32(a.tab, a.log2dt, &tab);
-  __syncthreads();
-  const unsigned n = *((volatile unsigned*)&a.hdr[kHdrMedium]);
-  const unsigned stride = gridDim.x * blockDim.x;
-  const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
-    const bool in = i < n;
-    int w = 0;
-    if (in) {
-      const unsigned lh = __ldcs(a.rec_lohi + i);
-      w = (lh >> 8) - (lh & 0xff) + 1;
-    }
-    const int WMw = __reduce_max_sync(kFull, w);
-    if (WMw <= 2)
-      medium_cell<2>(a, tab, i, in);
-    else if (WMw <= 4)
-      medium_cell<4>(a, tab, i, in);
-    else
-      medium_cell<6>(a, tab, i, in);
-  }
-}
-
-// Stiff records (a rate with W dt > 1) and the tail cells, one per thread:
-// the full path of finish_cell (which may queue the cell for FP64
-// coefficients).  They fill the record arrays from the back.
+// The stiff-cell records, one per thread.
 template <int W>
 __device__ __forceinline__ bool record_cell(const StepArgs& a, const StagedF32& tab,
-                                            int64_t i, int c, float Ec, int lo,
+                                            unsigned i, int c, float Ec, int lo,
                                             int hi) {
   float v[W];
 #pragma unroll
@@ -698,11 +587,10 @@ __global__ void __launch_bounds__(256)
   const unsigned n = *((volatile unsigned*)&a.hdr[kHdrStiff]);
   const unsigned stride = gridDim.x * blockDim.x;
   const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n_up; k += stride) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
     bool fb = false;
     int c = 0;
-    if (k < n) {
-      const int64_t i = a.rec_cap - 1 - (int64_t)k;
+    if (i < n) {
       c = (int)__ldcs(a.rec_c + i);
       const float Ec = __ldcs(a.rec_E + i);
       const unsigned lh = __ldcs(a.rec_lohi + i);
@@ -869,8 +757,6 @@ cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s) {
   const int64_t cap = (int64_t)resident_blocks_f32() * num_sms;
   const int blocks = (int)(need < cap ? need : cap);
   ion_step_f32_kernel<<<blocks, kWarps * 32, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ion_step_f32_medium_kernel<<<4 * num_sms, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ion_step_f32_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -268,9 +268,7 @@ def counters(ws: torch.Tensor):
     return int(h[0]), int(h[1])
 
 
-def stiff_cells(ws: torch.Tensor):
-    """(cells finished in the Taylor form on the long path, cells finished
-    in the Bateman form) of the last FP32 step that used `ws`: the cells with
-    some W dt > 0.025, split at max W dt = 1; synchronizes."""
-    h = ws[8:16].cpu().view(torch.int32)
-    return int(h[0]), int(h[1])
+def stiff_cells(ws: torch.Tensor) -> int:
+    """Cells of the last FP32 step that used `ws` with some W dt > 0.025,
+    finished on the long path; synchronizes."""
+    return int(ws[8:12].cpu().view(torch.int32)[0])

@@ -37,7 +37,7 @@ def main():
             ionize.step(sp, wl.E, wl.N, wl.lo, wl.hi, 0.05, dne, ws=ws)
         torch.cuda.synchronize()
         print("f32: fp64-coefficient cells, invalid windows:", ionize.counters(ws),
-              "long-path cells (Taylor, Bateman):", ionize.stiff_cells(ws))
+              "stiff cells:", ionize.stiff_cells(ws))
     if args.form in ("f64", "both"):
         E64, N64 = wl.E.double(), N0.double()
         dne64 = torch.empty(n, dtype=torch.float64, device=dev)
