@@ -119,8 +119,8 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
               int k_hi, void* W_out, int64_t ldw, int dtype, void* stream);
 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
- * a 256-byte header plus, for ION_F32, 38 bytes per cell: a 4-byte queue
- * slot (cells whose Bateman coefficients are computed in FP64) and a 34-byte
+ * a 256-byte header plus, for ION_F32, 40 bytes per cell: a 5-byte queue
+ * slot (cells whose Bateman coefficients are computed in FP64) and a 35-byte
  * record (cells with a rate W dt > 0.025, finished by a second kernel from
  * the inputs the first one loaded). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
@@ -171,6 +171,62 @@ ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
              void* dne, const void* n_gas, const ion_step_opts* opts, int flags,
              void* workspace, size_t workspace_bytes, void* stream);
 
+/* One species' cells for ion_step_batched: the arguments of ion_step that
+ * belong to a species.  The jobs of one call must not share cells. */
+typedef struct {
+  const ion_species* species;
+  const void* E;
+  void* N;
+  int64_t ld;
+  int64_t ncells;
+  uint8_t* k_lo;
+  uint8_t* k_hi;
+  void* dne;
+  const void* n_gas;
+} ion_batch_job;
+
+/* Launch shape of the FP32 streaming kernel: cells per lane (1, 2 or 4),
+ * warps per block (2, 4 or 8), resident blocks per SM (0: as many as fit).
+ * NULL selects {4, 4, 0}. */
+typedef struct {
+  int cells_per_lane;
+  int warps_per_block;
+  int blocks_per_sm;
+} ion_launch_shape;
+
+/* Maximum number of jobs of one ion_step_batched call. */
+#define ION_MAX_JOBS 8
+
+/* Workspace bytes of ion_step_batched: ion_step_workspace_bytes of the total
+ * cell count of the jobs. */
+ION_API size_t ion_step_batched_workspace_bytes(const ion_batch_job* jobs, int njobs,
+                                                int flags);
+
+/* ion_step_batched -- ion_step for up to ION_MAX_JOBS species (different Z,
+ * cell counts and arrays) in one launch: with ION_F32 one persistent kernel
+ * walks the cells of every job (each warp picks its job per chunk of cells)
+ * and the follow-up kernels serve all jobs; with ION_F64_PLAIN one kernel per
+ * job is launched.  Each job obeys the rules of ion_step's arguments; dt,
+ * opts and flags apply to all.  `shape` chooses the launch shape (NULL: the
+ * default; ion_autotune finds the fastest).  The total cell count must stay
+ * below 2^31.  Errors as ion_step. */
+ION_API int ion_step_batched(const ion_batch_job* jobs, int njobs, double dt_fs,
+                             const ion_step_opts* opts, int flags,
+                             const ion_launch_shape* shape, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
+/* ion_autotune -- times ion_step_batched (ION_F32) on the given jobs for every
+ * built launch shape (cells per lane x warps per block x blocks per SM) and
+ * returns the shape with the smallest median time over `reps` (1..64) timed
+ * steps, and that time in ms (best_ms may be NULL).  It runs real steps on
+ * the jobs' arrays, so pass copies of the state.  It creates CUDA events and
+ * synchronizes on them: call it outside any stream capture.  Errors: those
+ * of ion_step_batched, ION_EINVAL for ION_F64_PLAIN or a bad reps. */
+ION_API int ion_autotune(const ion_batch_job* jobs, int njobs, double dt_fs,
+                         const ion_step_opts* opts, int flags, void* workspace,
+                         size_t workspace_bytes, int reps, void* stream,
+                         ion_launch_shape* best, float* best_ms);
+
 /* ion_step_noalloc -- ion_step for callers that cannot allocate device
  * memory.  Some callers cannot make a device allocation at the point where
  * they step the populations: code that runs while a CUDA graph is being
@@ -196,7 +252,7 @@ ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
  * Errors: those of ion_step, plus ION_EINVAL for ncells beyond the maximum
  * and ION_ECUDA if the array's address cannot be obtained. */
 #define ION_STEP_NOALLOC_MAX_CELLS 262144
-#define ION_STEP_NOALLOC_SCRATCH_BYTES 9961728
+#define ION_STEP_NOALLOC_SCRATCH_BYTES 10486016
 ION_API int ion_step_noalloc(const ion_species* sp, const void* E, void* N,
                              int64_t ld, int64_t ncells, double dt_fs,
                              uint8_t* k_lo, uint8_t* k_hi, void* dne,

@@ -218,12 +218,11 @@ size_t ion_step_workspace_bytes(int64_t ncells, int flags) {
   return ion::step_workspace_bytes(ncells, (flags & ION_F64_PLAIN) != 0);
 }
 
-int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
-             int64_t ncells, double dt_fs, uint8_t* k_lo, uint8_t* k_hi,
-             void* dne, const void* n_gas, const ion_step_opts* opts, int flags,
-             void* workspace, size_t workspace_bytes, void* stream) {
-  int rc = check_species(sp);
-  if (rc) return rc;
+}  // extern "C"
+
+namespace {
+
+int check_flags(int flags) {
   const int known = ION_F64_PLAIN | ION_NO_WINDOW_UPDATE | ION_NO_FP64_FALLBACK |
                     ION_FORCE_FP64_COEF;
   if (flags & ~known) return fail(ION_EINVAL, "unknown flag bits 0x%x", flags & ~known);
@@ -232,8 +231,10 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
     return fail(ION_EINVAL, "fallback flags apply to ION_F32 only");
   if ((flags & ION_NO_FP64_FALLBACK) && (flags & ION_FORCE_FP64_COEF))
     return fail(ION_EINVAL, "ION_NO_FP64_FALLBACK and ION_FORCE_FP64_COEF exclude each other");
-  if (ncells < 0 || ncells >= (int64_t(1) << 31))
-    return fail(ION_EINVAL, "ncells=%lld outside [0, 2^31)", (long long)ncells);
+  return ION_OK;
+}
+
+int make_policy(double dt_fs, const ion_step_opts* opts, int flags, ion::Policy* pol) {
   if (!(dt_fs >= 0.0) || !std::isfinite(dt_fs))
     return fail(ION_EINVAL, "dt_fs must be finite and >= 0 (got %g)", dt_fs);
   ion_step_opts o = {1e-6, 1e-3};
@@ -242,44 +243,193 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
     return fail(ION_EINVAL, "eps_shift must be finite and >= 0");
   if (!(o.degen_gap >= 0.0) || !(o.degen_gap < 1.0))
     return fail(ION_EINVAL, "degen_gap must lie in [0, 1)");
-  if (!workspace) return fail(ION_EINVAL, "workspace is NULL");
-  const size_t need = ion_step_workspace_bytes(ncells, flags);
-  if (workspace_bytes < need)
-    return fail(ION_EINVAL, "workspace has %zu bytes, %zu needed", workspace_bytes, need);
-  if (!aligned(workspace, 256)) return fail(ION_EINVAL, "workspace must be 256-byte aligned");
+  pol->zero_dt = dt_fs == 0.0;
+  pol->log2dt = dt_fs > 0.0 ? std::log2(dt_fs) : 0.0;
+  pol->eps = o.eps_shift;
+  pol->gap = o.degen_gap;
+  pol->flags = flags;
+  return ION_OK;
+}
+
+// Checks one job's arrays and fills its JobIO (Q: cells per lane of the
+// FP32 launch, for the alignment of vector copies).
+int make_job(const ion_species* sp, const void* E, void* N, int64_t ld, int64_t ncells,
+             uint8_t* k_lo, uint8_t* k_hi, void* dne, const void* n_gas, bool f64, int Q,
+             const char* who, ion::JobIO* J) {
+  int rc = check_species(sp);
+  if (rc) return rc;
+  if (ncells < 0 || ncells >= (int64_t(1) << 31))
+    return fail(ION_EINVAL, "%s: ncells=%lld outside [0, 2^31)", who, (long long)ncells);
   if (ncells > 0) {
     if (!E || !N || !k_lo || !k_hi || !dne)
-      return fail(ION_EINVAL, "E, N, k_lo, k_hi and dne must be non-NULL");
-    if (ld < ncells) return fail(ION_EINVAL, "ld=%lld < ncells", (long long)ld);
-    if (ld > (int64_t(1) << 40)) return fail(ION_EINVAL, "ld too large");
+      return fail(ION_EINVAL, "%s: E, N, k_lo, k_hi and dne must be non-NULL", who);
+    if (ld < ncells) return fail(ION_EINVAL, "%s: ld=%lld < ncells", who, (long long)ld);
+    if (ld > (int64_t(1) << 40)) return fail(ION_EINVAL, "%s: ld too large", who);
     const size_t el = f64 ? 8 : 4;
     if (!aligned(E, el) || !aligned(N, el) || !aligned(dne, el) ||
         (n_gas && !aligned(n_gas, el)))
-      return fail(ION_EINVAL, "E, N, dne and n_gas must be aligned to their element size");
+      return fail(ION_EINVAL, "%s: E, N, dne and n_gas must be aligned to their element size",
+                  who);
     if (!f64 && (!aligned(k_lo, 4) || !aligned(k_hi, 4)))
-      return fail(ION_EINVAL, "k_lo and k_hi must be 4-byte aligned");
+      return fail(ION_EINVAL, "%s: k_lo and k_hi must be 4-byte aligned", who);
   }
-  ion::StepArgs a;
-  a.tab = sp->dev;
-  a.Z = sp->Z;
-  a.E = E;
-  a.N = N;
-  a.ld = ld;
-  a.ncells = (int)ncells;
-  a.zero_dt = dt_fs == 0.0;
-  a.log2dt = dt_fs > 0.0 ? std::log2(dt_fs) : 0.0;
-  a.lo = k_lo;
-  a.hi = k_hi;
-  a.dne = dne;
-  a.n_gas = n_gas;
-  a.eps = o.eps_shift;
-  a.gap = o.degen_gap;
-  a.flags = flags;
-  a.vec = aligned(E, 16) && aligned(N, 16) && aligned(dne, 16) && (ld % 4) == 0;
-  ion::bind_workspace(a, workspace);
+  J->tab = sp->dev;
+  J->Z = sp->Z;
+  J->E = E;
+  J->N = N;
+  J->ld = ld;
+  J->ncells = (int)ncells;
+  J->lo = k_lo;
+  J->hi = k_hi;
+  J->dne = dne;
+  J->n_gas = n_gas;
+  J->chunk0 = 0;
+  const size_t vb = 4 * (size_t)Q;
+  J->vec = aligned(E, vb) && aligned(N, vb) && aligned(dne, vb) && (ld % Q) == 0;
+  return ION_OK;
+}
+
+int check_workspace(void* workspace, size_t have, size_t need) {
+  if (!workspace) return fail(ION_EINVAL, "workspace is NULL");
+  if (have < need) return fail(ION_EINVAL, "workspace has %zu bytes, %zu needed", have, need);
+  if (!aligned(workspace, 256)) return fail(ION_EINVAL, "workspace must be 256-byte aligned");
+  return ION_OK;
+}
+
+int run_batch(const ion_batch_job* jobs, int njobs, double dt_fs, const ion_step_opts* opts,
+              int flags, const ion_launch_shape* shape, void* workspace, size_t ws_bytes,
+              void* stream) {
+  if (njobs < 1 || njobs > ion::kMaxJobs)
+    return fail(ION_EINVAL, "njobs=%d outside [1, %d]", njobs, ion::kMaxJobs);
+  if (!jobs) return fail(ION_EINVAL, "jobs is NULL");
+  int rc = check_flags(flags);
+  if (rc) return rc;
+  ion::LaunchShape sh = ion::default_shape();
+  if (shape) {
+    sh = {shape->cells_per_lane, shape->warps_per_block, shape->blocks_per_sm};
+    if (!ion::valid_shape(sh))
+      return fail(ION_EINVAL,
+                  "launch shape (%d cells/lane, %d warps/block, %d blocks/SM) is not built",
+                  sh.cells_per_lane, sh.warps_per_block, sh.blocks_per_sm);
+  }
+  const bool f64 = (flags & ION_F64_PLAIN) != 0;
+  ion::BatchArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.njobs = njobs;
+  if ((rc = make_policy(dt_fs, opts, flags, &a.pol))) return rc;
+  int64_t total = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const ion_batch_job& b = jobs[j];
+    char who[32];
+    snprintf(who, sizeof who, "job %d", j);
+    if ((rc = make_job(b.species, b.E, b.N, b.ld, b.ncells, b.k_lo, b.k_hi, b.dne, b.n_gas,
+                       f64, sh.cells_per_lane, who, &a.job[j])))
+      return rc;
+    if (b.species->device != jobs[0].species->device)
+      return fail(ION_EINVAL, "job %d: its species lives on another device", j);
+    total += b.ncells;
+  }
+  if (total >= (int64_t(1) << 31))
+    return fail(ION_EINVAL, "%lld cells in one call; the limit is 2^31 - 1", (long long)total);
+  if ((rc = check_workspace(workspace, ws_bytes, ion::step_workspace_bytes(total, f64))))
+    return rc;
+  ion::bind_workspace(a.ws, workspace, total);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = f64 ? ion::launch_step_f64(a, s) : ion::launch_step_f32(a, sp->num_sms, s);
+  cudaError_t e;
+  if (f64) {
+    e = cudaMemsetAsync(a.ws.hdr, 0, ion::kHdrWords * sizeof(uint32_t), s);
+    for (int j = 0; j < njobs && e == cudaSuccess; ++j)
+      e = ion::launch_step_f64(a.job[j], a.pol, a.ws.hdr, s);
+  } else {
+    e = ion::launch_batch_f32(a, sh, jobs[0].species->num_sms, s);
+  }
   return e == cudaSuccess ? ok() : cuda_fail(e, "ion_step launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ion_step_batched_workspace_bytes(const ion_batch_job* jobs, int njobs, int flags) {
+  int64_t total = 0;
+  for (int j = 0; jobs && j < njobs; ++j) total += jobs[j].ncells > 0 ? jobs[j].ncells : 0;
+  return ion::step_workspace_bytes(total, (flags & ION_F64_PLAIN) != 0);
+}
+
+int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld, int64_t ncells,
+             double dt_fs, uint8_t* k_lo, uint8_t* k_hi, void* dne, const void* n_gas,
+             const ion_step_opts* opts, int flags, void* workspace, size_t workspace_bytes,
+             void* stream) {
+  int rc = check_species(sp);
+  if (rc) return rc;
+  const ion_batch_job job = {sp, E, N, ld, ncells, k_lo, k_hi, dne, n_gas};
+  return run_batch(&job, 1, dt_fs, opts, flags, nullptr, workspace, workspace_bytes, stream);
+}
+
+int ion_step_batched(const ion_batch_job* jobs, int njobs, double dt_fs,
+                     const ion_step_opts* opts, int flags, const ion_launch_shape* shape,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+  return run_batch(jobs, njobs, dt_fs, opts, flags, shape, workspace, workspace_bytes, stream);
+}
+
+int ion_autotune(const ion_batch_job* jobs, int njobs, double dt_fs, const ion_step_opts* opts,
+                 int flags, void* workspace, size_t workspace_bytes, int reps, void* stream,
+                 ion_launch_shape* best, float* best_ms) {
+  if (!best) return fail(ION_EINVAL, "best is NULL");
+  if (flags & ION_F64_PLAIN) return fail(ION_EINVAL, "ion_autotune tunes the FP32 form only");
+  if (reps < 1 || reps > 64) return fail(ION_EINVAL, "reps=%d outside [1, 64]", reps);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "ion_autotune events");
+  float best_t = -1.0f;
+  ion_launch_shape bs = {0, 0, 0};
+  const int Qs[] = {1, 2, 4}, Ws[] = {2, 4, 8}, Bs[] = {0, 1, 2, 3, 4};
+  int rc = ION_OK;
+  for (int Q : Qs) {
+    for (int W : Ws) {
+      for (int B : Bs) {
+        const ion_launch_shape sh = {Q, W, B};
+        // one untimed launch, then the median of `reps` timed ones
+        rc = run_batch(jobs, njobs, dt_fs, opts, flags, &sh, workspace, workspace_bytes, stream);
+        if (rc) break;
+        float ts[64];
+        for (int r = 0; r < reps && rc == ION_OK; ++r) {
+          cudaEventRecord(e0, s);
+          rc = run_batch(jobs, njobs, dt_fs, opts, flags, &sh, workspace, workspace_bytes,
+                         stream);
+          cudaEventRecord(e1, s);
+          if (rc) break;
+          if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+            rc = cuda_fail(e, "ion_autotune");
+            break;
+          }
+          cudaEventElapsedTime(&ts[r], e0, e1);
+        }
+        if (rc) break;
+        for (int i = 1; i < reps; ++i)  // insertion sort; reps is small
+          for (int k = i; k > 0 && ts[k] < ts[k - 1]; --k) {
+            const float t = ts[k];
+            ts[k] = ts[k - 1];
+            ts[k - 1] = t;
+          }
+        const float med = ts[reps / 2];
+        if (best_t < 0.0f || med < best_t) {
+          best_t = med;
+          bs = sh;
+        }
+      }
+      if (rc) break;
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  *best = bs;
+  if (best_ms) *best_ms = best_t;
+  return ok();
 }
 
 }  // extern "C"

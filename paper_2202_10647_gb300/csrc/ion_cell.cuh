@@ -1,0 +1,176 @@
+// ion_cell.cuh -- per-cell device code shared by the FP32 and FP64 step
+// kernels: the full update of one cell (rates, Taylor or Bateman form, window
+// slide, stores), queue appends and cp.async helpers.
+#pragma once
+
+#include <cstdint>
+
+#include "ion_device.cuh"
+#include "ion_step.cuh"
+
+namespace ion {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ bool window_ok(int lo, int hi, int Z) {
+  return lo <= hi && hi <= Z && hi - lo + 1 <= ION_MAX_WINDOW;
+}
+
+// ---------------------------------------------------------------------------
+// cp.async (global -> shared; completion tracked per thread in commit
+// groups, no spin loop involved).
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem),
+                 "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Per-precision hooks of the generic cell code.
+struct F32Form {
+  using T = float;
+  using Staged = StagedF32;
+  using Field = FieldF32;
+  __device__ static Field field(float E) { return field_f32(E); }
+  __device__ static float rate(const StagedF32& t, int k, const Field& f) {
+    return rate_dt_f32(t, k, f);
+  }
+};
+
+struct F64Form {
+  using T = double;
+  using Staged = StagedF64;
+  struct Field {
+    double E;
+  };
+  __device__ static Field field(double E) { return {E}; }
+  __device__ static double rate(const StagedF64& t, int k, const Field& f) {
+    return rate_dt_f64(t, k, f.E);
+  }
+};
+
+// Warp-aggregated append of (value, tag) for the lanes with `take` set: one
+// atomic per warp.  Every lane of the warp calls this.
+__device__ __forceinline__ void warp_append(uint32_t* counter, uint32_t* queue,
+                                            uint8_t* tags, bool take, uint32_t value,
+                                            uint8_t tag) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(counter, (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, 0);
+  if (take) {
+    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
+    queue[i] = value;
+    if (tags) tags[i] = tag;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full update of one cell whose window populations v[0..w-1] are loaded
+// (w <= WM): rates, Taylor or Bateman form, window slide, stores.  Returns
+// true (and stores nothing) if the cell goes to the FP64 queue.
+// ---------------------------------------------------------------------------
+template <class F, int WM>
+__device__ __forceinline__ bool finish_cell(const JobIO& J, const Policy& pol,
+                                            const typename F::Staged& tab, int c,
+                                            typename F::T Ec, int lo, int hi,
+                                            typename F::T (&v)[WM], bool allow_fb) {
+  using T = typename F::T;
+  T* __restrict__ N = static_cast<T*>(J.N);
+  const int w = hi - lo + 1;
+  T dne = T(0);
+  int nlo = lo, nhi = hi;
+  if constexpr (WM >= 2) {
+    if (w >= 2) {
+      const typename F::Field f = F::field(Ec);
+      T lam[WM];
+      T lmax = T(0);
+#pragma unroll
+      for (int r = 0; r < WM; ++r) {
+        lam[r] = (r < w - 1 && !pol.zero_dt) ? F::rate(tab, lo + r, f) : T(0);
+        lmax = fmax(lmax, lam[r]);
+      }
+      if (lmax <= DDParams<T>::prop_max) {
+        dne = taylor_propagate<T, WM>(v, lam, w, lmax);
+      } else {
+        if (allow_fb && (pol.flags & ION_NO_FP64_FALLBACK) == 0 &&
+            ((pol.flags & ION_FORCE_FP64_COEF) != 0 ||
+             (pol.gap > 0.0 && near_degenerate<T, WM>(lam, w, (T)pol.gap))))
+          return true;
+        dne = dd_update<T, WM>(v, lam, w);
+      }
+      if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0)
+        slide_window<T, WM>(v, w, J.Z, (T)pol.eps, nlo, nhi);
+      T* p = N + (int64_t)lo * J.ld + c;
+#pragma unroll
+      for (int r = 0; r < WM; ++r) {
+        if (r < w) __stcs(p, v[r]);
+        p += J.ld;
+      }
+    }
+  }
+  const T* __restrict__ G = static_cast<const T*>(J.n_gas);
+  __stcs(static_cast<T*>(J.dne) + c, G ? dne * G[c] : dne);
+  if (nlo != lo) {
+    J.lo[c] = (uint8_t)nlo;
+    J.hi[c] = (uint8_t)nhi;
+  }
+  return false;
+}
+
+// The same, loading the window from global memory; W bounds the width.
+template <class F, int W>
+__device__ __forceinline__ bool global_cell(const JobIO& J, const Policy& pol,
+                                            const typename F::Staged& tab, int c,
+                                            typename F::T Ec, int lo, int hi,
+                                            bool allow_fb) {
+  using T = typename F::T;
+  const T* __restrict__ N = static_cast<const T*>(J.N);
+  T v[W];
+  const T* p = N + (int64_t)lo * J.ld + c;
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    v[r] = r < hi - lo + 1 ? __ldcs(p) : T(0);
+    p += J.ld;
+  }
+  return finish_cell<F, W>(J, pol, tab, c, Ec, lo, hi, v, allow_fb);
+}
+
+// Dispatch on a width known to be 1..6 (per-lane switch).
+template <class F>
+__device__ __forceinline__ bool global_cell_any(const JobIO& J, const Policy& pol,
+                                                const typename F::Staged& tab, int c,
+                                                typename F::T Ec, int lo, int hi,
+                                                bool allow_fb) {
+  switch (hi - lo + 1) {
+    case 1:
+      return global_cell<F, 1>(J, pol, tab, c, Ec, lo, hi, allow_fb);
+    case 2:
+      return global_cell<F, 2>(J, pol, tab, c, Ec, lo, hi, allow_fb);
+    case 3:
+      return global_cell<F, 3>(J, pol, tab, c, Ec, lo, hi, allow_fb);
+    case 4:
+      return global_cell<F, 4>(J, pol, tab, c, Ec, lo, hi, allow_fb);
+    case 5:
+      return global_cell<F, 5>(J, pol, tab, c, Ec, lo, hi, allow_fb);
+    default:
+      return global_cell<F, 6>(J, pol, tab, c, Ec, lo, hi, allow_fb);
+  }
+}
+
+}  // namespace ion

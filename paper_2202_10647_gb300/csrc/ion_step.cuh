@@ -16,44 +16,80 @@ constexpr int kHdrStiff = 2;     // stiff-cell records written by the streaming 
 constexpr int kHdrWords = 3;
 constexpr size_t kHdrBytes = 256;
 
-struct StepArgs {
+// Largest number of species one batched launch advances.
+constexpr int kMaxJobs = 8;
+
+// Where one job's cells live.
+struct JobIO {
   const SpeciesTable* tab;
   int Z;
   const void* E;
   void* N;
   int64_t ld;
   int ncells;
-  double log2dt;
-  int zero_dt;
   uint8_t* lo;
   uint8_t* hi;
   void* dne;
   const void* n_gas;
+  int chunk0;  // first chunk of this job in the launch's chunk numbering
+  int vec;     // E, N, dne aligned for vector copies of a lane's cells
+};
+
+// Per-call policy shared by all jobs.
+struct Policy {
+  double log2dt;
+  int zero_dt;
   double eps;
   double gap;
   int flags;
-  int vec;          // E, N 16-byte aligned and ld % 4 == 0: 16-byte copies
-  uint32_t* hdr;    // workspace header (kHdr* words)
-  uint32_t* queue;  // cells for the FP64-coefficient kernel
-  // stiff-cell records (FP32 form): cell, |E|, lo | hi << 8, window planes
+};
+
+// Workspace views.
+struct Scratch {
+  uint32_t* hdr;      // kHdr* words
+  uint32_t* queue;    // FP64-coefficient cells
+  uint8_t* queue_job;
+  // stiff-cell records: cell, job, |E|, lo | hi << 8, window planes
   // rec_V[r * rec_cap + i]
   uint32_t* rec_c;
+  uint8_t* rec_job;
   float* rec_E;
   uint16_t* rec_lohi;
   float* rec_V;
   int64_t rec_cap;
 };
 
-// Workspace layout (step.cu).
+struct BatchArgs {
+  int njobs;
+  int nchunks;  // full chunks over all jobs
+  JobIO job[kMaxJobs];
+  Policy pol;
+  Scratch ws;
+};
+
+// Launch shape of the FP32 streaming kernel (chosen by default or by
+// ion_autotune).
+struct LaunchShape {
+  int cells_per_lane;   // 1, 2 or 4
+  int warps_per_block;  // 2, 4 or 8
+  int blocks_per_sm;    // 0: as many as fit
+};
+
+// Workspace layout (step_f32.cu).
 size_t step_workspace_bytes(int64_t ncells, bool f64);
-void bind_workspace(StepArgs& a, void* ws);
+void bind_workspace(Scratch& s, void* ws, int64_t ncells);
 
 // Sets the calling thread's ion_last_error() message and returns `code`
 // (api.cu).
 int set_error(int code, const char* fmt, ...);
 
-// Launchers (step.cu).  They only enqueue; the caller has validated.
-cudaError_t launch_step_f32(const StepArgs& a, int num_sms, cudaStream_t s);
-cudaError_t launch_step_f64(const StepArgs& a, cudaStream_t s);
+// Launchers.  They only enqueue; the caller has validated.  `a.job[j].chunk0`
+// and `a.nchunks` are filled in by launch_batch_f32.
+cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms,
+                             cudaStream_t s);
+cudaError_t launch_step_f64(const JobIO& job, const Policy& pol, uint32_t* hdr,
+                            cudaStream_t s);
+LaunchShape default_shape();
+bool valid_shape(const LaunchShape& s);
 
 }  // namespace ion

@@ -1,0 +1,715 @@
+// step_f32.cu -- the FP32 form of ion_step / ion_step_batched (ION_F32):
+// one persistent launch over the cells of up to kMaxJobs species, then two
+// small kernels over the cells it left behind.
+//
+//   ion_stream_kernel<Q, W>  every warp walks its own sequence of chunks of
+//       32*Q cells (Q consecutive cells per lane) through a 3-stage ring in
+//       shared memory.  cp.async brings |E|, k_lo and k_hi in two chunks
+//       ahead and each lane's own window planes one chunk ahead (one copy of
+//       4*Q bytes per plane when the lane's cells share their window), so the
+//       loads in flight cost no registers and the traffic is exactly the
+//       cells' windows.  A cell whose rates all have W dt <= 0.025 is
+//       finished here (at most four Taylor terms of exp(dt A)).  The others
+//       ("stiff" cells) write the inputs already loaded into a record queue:
+//       in a laser field |E| swings from zero to its peak every few cells, so
+//       most warps near the pulse hold a few stiff cells, and finishing them
+//       in place would make every such warp run the longest path of its
+//       lanes.  The window-width bucket (the loops' bound) is taken per warp
+//       and chunk.  Q and W (warps per block) are the launch shape that
+//       ion_autotune picks.
+//   ion_stiff_kernel   the records, one per thread in full warps: Taylor form
+//       up to W dt <= 1, divided-difference (Bateman) form above.  Cells with
+//       a nearly degenerate rate pair are left untouched and queued for
+//   ion_fb_kernel      FP32 rates, FP64 Bateman coefficients and propagation,
+//       rounded back to FP32.
+//
+// One step is Eqs. 1-9 of the paper per cell; see ion_device.cuh.
+#include <cstdint>
+
+#include "ion_cell.cuh"
+#include "ion_step.cuh"
+
+namespace ion {
+
+namespace {
+
+constexpr int kStages = 3;
+constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms
+constexpr int kEasyTerms = 4;
+
+template <int Q>
+struct VecOf;
+template <>
+struct VecOf<1> {
+  using T = float;
+};
+template <>
+struct VecOf<2> {
+  using T = float2;
+};
+template <>
+struct VecOf<4> {
+  using T = float4;
+};
+
+__device__ __forceinline__ float vget(const float& x, int) { return x; }
+__device__ __forceinline__ float vget(const float2& x, int j) { return j == 0 ? x.x : x.y; }
+__device__ __forceinline__ float vget(const float4& x, int j) {
+  return j == 0 ? x.x : j == 1 ? x.y : j == 2 ? x.z : x.w;
+}
+__device__ __forceinline__ void vstore(float* p, const float (&v)[1]) { __stcs(p, v[0]); }
+__device__ __forceinline__ void vstore(float* p, const float (&v)[2]) {
+  __stcs(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+}
+__device__ __forceinline__ void vstore(float* p, const float (&v)[4]) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+
+template <int Q>
+struct QStage {
+  using V = typename VecOf<Q>::T;
+  V E[32];                      // |E| of the lane's Q cells
+  uint32_t lo[8 * Q];           // k_lo of the chunk's 32*Q cells
+  uint32_t hi[8 * Q];           // k_hi
+  V P[ION_MAX_WINDOW][32];      // P[r][lane] component j = N[lo_j + r] of cell j
+};
+
+// The Q bytes of a lane in a packed byte array, and whether they are equal.
+template <int Q>
+__device__ __forceinline__ uint32_t lane_bytes(const uint32_t* arr, int lane) {
+  if constexpr (Q == 4) return arr[lane];
+  if constexpr (Q == 2) return (arr[lane >> 1] >> (16 * (lane & 1))) & 0xffffu;
+  return (arr[lane >> 2] >> (8 * (lane & 3))) & 0xffu;
+}
+template <int Q>
+__device__ __forceinline__ bool bytes_equal(uint32_t x) {
+  if constexpr (Q == 4) return x == (x & 0xff) * 0x01010101u;
+  if constexpr (Q == 2) return x == (x & 0xff) * 0x0101u;
+  return true;
+}
+
+// Job of a chunk (jobs are few; chunks are numbered job after job).
+__device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
+  int j = 0;
+#pragma unroll
+  for (int i = 1; i < kMaxJobs; ++i)
+    if (i < a.njobs && g >= a.job[i].chunk0) j = i;
+  return j;
+}
+
+// Appends the record of a stiff cell (one atomic per warp).  Every lane of
+// the warp calls this; `take` lanes pass their cell's inputs.
+__device__ __forceinline__ void append_record(const Scratch& S, bool take, int job,
+                                              int c, float Ec, int lo, int hi,
+                                              const float* v) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(&S.hdr[kHdrStiff], (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, 0);
+  if (take) {
+    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
+    S.rec_c[i] = (uint32_t)c;
+    S.rec_job[i] = (uint8_t)job;
+    S.rec_E[i] = Ec;
+    S.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
+    const int w = hi - lo + 1;
+#pragma unroll
+    for (int r = 0; r < ION_MAX_WINDOW; ++r)
+      if (r < w) S.rec_V[(int64_t)r * S.rec_cap + i] = v[r];
+  }
+}
+
+// Easy path of the lane's Q cells (c0..c0+Q-1 of job J, window bound WM).
+// Every lane of the warp calls this.  Cells whose rates all have
+// W dt <= kLamEasy are finished; stiff[j] marks the others, left untouched.
+// Every window rate takes the plain FP32 exponent y = (a_hi + a_lo) -
+// b log2|E| - C/|E|: its error is below ~6e-5 in log2 units even for terms of
+// 10^3, i.e. a relative error of W dt below 4e-5, which moves populations by
+// at most 0.025 * 4e-5 = 1e-6 in the cells this path finishes (the stiff
+// path recomputes its rates in float-float).  The Taylor series runs the
+// warp's largest term count (extra terms only add accuracy).
+template <int Q, int WM>
+__device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
+                                           const StagedF32& tab, const QStage<Q>& st,
+                                           int lane, int c0, const float (&Ev)[Q],
+                                           const int (&lo)[Q], const int (&hi)[Q],
+                                           const bool (&ok)[Q], bool uni, bool (&stiff)[Q]) {
+  int w[Q];
+  float v[Q][WM];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) w[j] = ok[j] ? hi[j] - lo[j] + 1 : 0;
+#pragma unroll
+  for (int r = 0; r < WM; ++r) {
+    const typename VecOf<Q>::T p = st.P[r][lane];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) v[j][r] = vget(p, j);  // r >= w: ignored
+  }
+  float lam[Q][WM];
+  int Rl = 0;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    stiff[j] = false;
+#pragma unroll
+    for (int r = 0; r < WM; ++r) lam[j][r] = 0.0f;
+    const FieldF32 f = field_f32(Ev[j]);
+    const bool live = w[j] >= 2 && !f.zero && !pol.zero_dt;
+    const int base = ok[j] ? lo[j] : 0;
+#pragma unroll
+    for (int r = 0; r < WM - 1; ++r) {
+      const float4 h = tab.hi[min(base + r, ION_MAX_Z)];
+      const float q = h.z * f.rE;
+      const float y = (fmaf(-h.y, f.lg, h.x) - q) + h.w;
+      const bool on = live && r < w[j] - 1 && q <= (float)kCutoffLog2;
+      lam[j][r] = on ? ex2_approx(fminf(y, 99.0f)) : 0.0f;
+    }
+    float lmax = 0.0f;
+#pragma unroll
+    for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
+    stiff[j] = lmax > kLamEasy;
+    const float x = stiff[j] ? 0.0f : 2.0f * lmax;
+    int R = 0;
+#pragma unroll
+    for (int i = 0; i < kEasyTerms; ++i) R += x > kThrF32[i] ? 1 : 0;
+    Rl = max(Rl, R);
+  }
+  const int Rw = __reduce_max_sync(kFull, Rl);
+  float dne[Q];
+  int nlo[Q], nhi[Q];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    dne[j] = 0.0f;
+    nlo[j] = lo[j];
+    nhi[j] = hi[j];
+    if (stiff[j] || w[j] < 2) continue;
+    float t[WM], inc[WM];
+#pragma unroll
+    for (int i = 0; i < WM; ++i) {
+      t[i] = i < w[j] ? v[j][i] : 0.0f;
+      inc[i] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 1; k <= kEasyTerms; ++k) {
+      if (k > Rw) break;
+      const float rk = 1.0f / k;
+#pragma unroll
+      for (int i = WM - 1; i >= 0; --i) {
+        const float gain = i > 0 ? lam[j][i - 1] * t[i - 1] : 0.0f;
+        t[i] = (gain - lam[j][i] * t[i]) * rk;
+        inc[i] += t[i];
+      }
+    }
+    float cum = 0.0f;
+#pragma unroll
+    for (int r = 0; r < WM - 1; ++r) {
+      if (r < w[j] - 1) {
+        cum -= inc[r];  // population that left states <= r
+        dne[j] += cum;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < WM; ++r) v[j][r] += inc[r];
+    if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0 && v[j][0] < (float)pol.eps && hi[j] < J.Z)
+      slide_window<float, WM>(v[j], w[j], J.Z, (float)pol.eps, nlo[j], nhi[j]);
+  }
+  // stores
+  const float* __restrict__ G = static_cast<const float*>(J.n_gas);
+  if (G) {
+#pragma unroll
+    for (int j = 0; j < Q; ++j)
+      if (ok[j] && !stiff[j]) dne[j] *= G[c0 + j];
+  }
+  bool whole = uni;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) whole = whole && !stiff[j];
+  float* __restrict__ N = static_cast<float*>(J.N);
+  float* __restrict__ D = static_cast<float*>(J.dne);
+  if (whole && J.vec) {
+    float* p = N + (int64_t)lo[0] * J.ld + c0;
+#pragma unroll
+    for (int r = 0; r < WM; ++r) {
+      if (r < w[0]) {
+        float o[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) o[j] = v[j][r];
+        vstore(p, o);
+      }
+      p += J.ld;
+    }
+    vstore(D + c0, dne);
+  } else {
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      if (!ok[j] || stiff[j]) continue;
+      float* p = N + (int64_t)lo[j] * J.ld + c0 + j;
+#pragma unroll
+      for (int r = 0; r < WM; ++r) {
+        if (r < w[j]) __stcs(p, v[j][r]);
+        p += J.ld;
+      }
+      __stcs(D + c0 + j, dne[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    if (ok[j] && !stiff[j] && nlo[j] != lo[j]) {
+      J.lo[c0 + j] = (uint8_t)nlo[j];
+      J.hi[c0 + j] = (uint8_t)nhi[j];
+    }
+  }
+}
+
+template <int Q>
+constexpr size_t stage_bytes() {
+  return sizeof(QStage<Q>);
+}
+
+template <int Q, int W>
+constexpr size_t stream_smem(int njobs) {
+  return (size_t)njobs * sizeof(StagedF32) + (size_t)W * kStages * sizeof(QStage<Q>);
+}
+
+template <int Q, int W>
+__global__ void __launch_bounds__(W * 32)
+    ion_stream_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  StagedF32* tabs = reinterpret_cast<StagedF32*>(smem);
+  QStage<Q>* ring = reinterpret_cast<QStage<Q>*>(smem + (size_t)a.njobs * sizeof(StagedF32));
+  for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
+  {
+    // plane slots past a cell's window are read (and ignored); keep them
+    // finite
+    float* z = reinterpret_cast<float*>(ring);
+    const int nz = (int)(W * kStages * sizeof(QStage<Q>) / sizeof(float));
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = 0.0f;
+  }
+  __syncthreads();
+
+  constexpr int kChunk = 32 * Q;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  QStage<Q>* S = ring + wib * kStages;
+  const int gw = blockIdx.x * W + wib;
+  const int TW = gridDim.x * W;
+  const int K = gw < a.nchunks ? (a.nchunks - 1 - gw) / TW + 1 : 0;
+  using V = typename VecOf<Q>::T;
+
+  // |E|, k_lo, k_hi of chunk k into stage sg (one commit group)
+  auto issue_front = [&](int k, int sg) {
+    if (k < K) {
+      const int g = gw + k * TW;
+      const JobIO& J = a.job[job_of(a, g)];
+      const int cb = (g - J.chunk0) * kChunk;
+      QStage<Q>& st = S[sg];
+      const float* E = static_cast<const float*>(J.E) + cb + Q * lane;
+      if (J.vec) {
+        cp_async<4 * Q>(&st.E[lane], E);
+      } else {
+        float* e = reinterpret_cast<float*>(&st.E[lane]);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) cp_async<4>(e + j, E + j);
+      }
+      if constexpr (Q == 4) {
+        cp_async<4>(&st.lo[lane], J.lo + cb + 4 * lane);
+        cp_async<4>(&st.hi[lane], J.hi + cb + 4 * lane);
+      } else {
+        constexpr int nw = 8 * Q;
+        if (lane < nw)
+          cp_async<4>(&st.lo[lane], J.lo + cb + 4 * lane);
+        else if (lane < 2 * nw)
+          cp_async<4>(&st.hi[lane - nw], J.hi + cb + 4 * (lane - nw));
+      }
+    }
+    cp_async_commit();
+  };
+  // the window planes of the lane's cells of chunk k in stage sg
+  auto issue_planes = [&](int k, int sg) {
+    if (k < K) {
+      const int g = gw + k * TW;
+      const JobIO& J = a.job[job_of(a, g)];
+      const int c0 = (g - J.chunk0) * kChunk + Q * lane;
+      QStage<Q>& st = S[sg];
+      const uint32_t l = lane_bytes<Q>(st.lo, lane), h = lane_bytes<Q>(st.hi, lane);
+      const int lo0 = l & 0xff, hi0 = h & 0xff;
+      const float* N = static_cast<const float*>(J.N);
+      if (J.vec && bytes_equal<Q>(l) && bytes_equal<Q>(h)) {
+        // the lane's cells share their window: one copy per plane
+        const int w = window_ok(lo0, hi0, J.Z) ? hi0 - lo0 + 1 : 0;
+        const float* p = N + (int64_t)lo0 * J.ld + c0;
+        V* d = &st.P[0][lane];
+        for (int r = 0; r < w; ++r) {
+          cp_async<4 * Q>(d, p);
+          p += J.ld;
+          d += 32;
+        }
+      } else {
+        float* P0 = reinterpret_cast<float*>(&st.P[0][lane]);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          const int lj = (l >> (8 * j)) & 0xff, hj = (h >> (8 * j)) & 0xff;
+          const int w = window_ok(lj, hj, J.Z) ? hj - lj + 1 : 0;
+          const float* p = N + (int64_t)lj * J.ld + c0 + j;
+          for (int r = 0; r < w; ++r) {
+            cp_async<4>(P0 + r * 32 * Q + j, p);
+            p += J.ld;
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  // chunk k lives in stage s0, k+1 in s1, k+2 in s2
+  int s0 = 0, s1 = 1, s2 = 2;
+  issue_front(0, s0);
+  issue_front(1, s1);
+  cp_async_wait<1>();  // front(0)
+  __syncwarp();
+  issue_planes(0, s0);
+  for (int k = 0; k < K; ++k) {
+    issue_front(k + 2, s2);
+    cp_async_wait<2>();  // front(k+1): pending are planes(k), front(k+2)
+    __syncwarp();
+    issue_planes(k + 1, s1);
+    cp_async_wait<2>();  // planes(k): pending are front(k+2), planes(k+1)
+    __syncwarp();
+
+    const QStage<Q>& st = S[s0];
+    const int g = gw + k * TW;
+    const int jid = job_of(a, g);
+    const JobIO& J = a.job[jid];
+    const int c0 = (g - J.chunk0) * kChunk + Q * lane;
+    const V e = st.E[lane];
+    float Ev[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) Ev[j] = vget(e, j);
+    const uint32_t l = lane_bytes<Q>(st.lo, lane), h = lane_bytes<Q>(st.hi, lane);
+    int lo[Q], hi[Q], wl = 0;
+    bool ok[Q];
+    bool uni;
+    if (bytes_equal<Q>(l) && bytes_equal<Q>(h)) {
+      const int l0 = l & 0xff, h0 = h & 0xff;
+      const bool o = window_ok(l0, h0, J.Z);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        lo[j] = l0;
+        hi[j] = h0;
+        ok[j] = o;
+      }
+      wl = o ? h0 - l0 + 1 : 0;
+      if (!o) atomicAdd(&a.ws.hdr[kHdrInvalid], (unsigned)Q);
+      uni = o;
+    } else {
+      int nbad = 0;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        lo[j] = (l >> (8 * j)) & 0xff;
+        hi[j] = (h >> (8 * j)) & 0xff;
+        ok[j] = window_ok(lo[j], hi[j], J.Z);
+        nbad += ok[j] ? 0 : 1;
+        wl = ok[j] ? max(wl, hi[j] - lo[j] + 1) : wl;
+      }
+      if (nbad) atomicAdd(&a.ws.hdr[kHdrInvalid], (unsigned)nbad);
+      uni = false;
+    }
+    const int WMw = __reduce_max_sync(kFull, wl);
+    bool stiff[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) stiff[j] = false;
+    const StagedF32& tab = tabs[jid];
+    if (WMw <= 1) {
+      float* D = static_cast<float*>(J.dne);
+#pragma unroll
+      for (int j = 0; j < Q; ++j)
+        if (ok[j]) __stcs(D + c0 + j, 0.0f);
+    } else if (WMw == 2) {
+      easy_cells<Q, 2>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+    } else if (WMw <= 4) {
+      easy_cells<Q, 4>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+    } else {
+      easy_cells<Q, 6>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+    }
+    // stiff cells: their inputs (as loaded) go to the record queue
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) any = any || stiff[j];
+    if (__ballot_sync(kFull, any)) {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        float vin[ION_MAX_WINDOW];
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = vget(st.P[r][lane], j);
+        append_record(a.ws, stiff[j], jid, c0 + j, Ev[j], lo[j], hi[j], vin);
+      }
+    }
+    __syncwarp();
+    const int t = s0;
+    s0 = s1;
+    s1 = s2;
+    s2 = t;
+  }
+  cp_async_wait<0>();
+
+  // each job's last, partial chunk (ncells % (32 Q) cells): every valid cell
+  // becomes a record for the stiff kernel, which runs the full path
+  for (int jid = 0; jid < a.njobs; ++jid) {
+    if (gw != (TW - 1 - jid % TW)) continue;
+    const JobIO& J = a.job[jid];
+    const int tail0 = (J.ncells / kChunk) * kChunk;
+    for (int cb = tail0; cb < J.ncells; cb += 32) {
+      const int c = cb + lane;
+      bool take = false;
+      float Ec = 0.0f, v[ION_MAX_WINDOW];
+      int lo = 0, hi = 0;
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = 0.0f;
+      if (c < J.ncells) {
+        Ec = static_cast<const float*>(J.E)[c];
+        lo = J.lo[c];
+        hi = J.hi[c];
+        take = window_ok(lo, hi, J.Z);
+        if (!take) atomicAdd(&a.ws.hdr[kHdrInvalid], 1u);
+        const float* p = static_cast<const float*>(J.N) + (int64_t)lo * J.ld + c;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+          if (take && r < hi - lo + 1) v[r] = p[0];
+          p += J.ld;
+        }
+      }
+      append_record(a.ws, take, jid, c, Ec, lo, hi, v);
+    }
+  }
+}
+
+// The stiff-cell records, one per thread.
+template <int W>
+__device__ __forceinline__ bool record_cell(const BatchArgs& a, const StagedF32& tab,
+                                            const JobIO& J, int64_t i, int c, float Ec,
+                                            int lo, int hi) {
+  float v[W];
+#pragma unroll
+  for (int r = 0; r < W; ++r) v[r] = __ldcs(a.ws.rec_V + (int64_t)r * a.ws.rec_cap + i);
+  return finish_cell<F32Form, W>(J, a.pol, tab, c, Ec, lo, hi, v, true);
+}
+
+__global__ void __launch_bounds__(256)
+    ion_stiff_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ StagedF32 tabs[kMaxJobs];
+  for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
+  __syncthreads();
+  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrStiff]);
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
+    bool fb = false;
+    int c = 0, jid = 0;
+    if (i < n) {
+      c = (int)__ldcs(a.ws.rec_c + i);
+      jid = a.ws.rec_job[i];
+      const JobIO& J = a.job[jid];
+      const float Ec = __ldcs(a.ws.rec_E + i);
+      const unsigned lh = __ldcs(a.ws.rec_lohi + i);
+      const int lo = lh & 0xff, hi = lh >> 8;
+      const StagedF32& tab = tabs[jid];
+      switch (hi - lo + 1) {
+        case 1:
+          fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi);
+          break;
+        case 2:
+          fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi);
+          break;
+        case 3:
+          fb = record_cell<3>(a, tab, J, i, c, Ec, lo, hi);
+          break;
+        case 4:
+          fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi);
+          break;
+        case 5:
+          fb = record_cell<5>(a, tab, J, i, c, Ec, lo, hi);
+          break;
+        default:
+          fb = record_cell<6>(a, tab, J, i, c, Ec, lo, hi);
+          break;
+      }
+    }
+    warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb, (uint32_t)c,
+                (uint8_t)jid);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64-coefficient pass over the queued cells, one cell per thread.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void fb_cell(const JobIO& J, const Policy& pol,
+                                        const StagedF32& tab, int c, int lo, int hi) {
+  float* __restrict__ N = static_cast<float*>(J.N);
+  const FieldF32 f = field_f32(static_cast<const float*>(J.E)[c]);
+  double v[W], lam[W];
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    v[r] = (double)N[(int64_t)(lo + r) * J.ld + c];
+    lam[r] = (r < W - 1 && !pol.zero_dt) ? (double)rate_dt_f32(tab, lo + r, f) : 0.0;
+  }
+  const double dne = dd_update<double, W>(v, lam, W);
+  float vf[W];
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    vf[r] = __double2float_rn(v[r]);
+    N[(int64_t)(lo + r) * J.ld + c] = vf[r];
+  }
+  int nlo = lo, nhi = hi;
+  if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0)
+    slide_window<float, W>(vf, W, J.Z, (float)pol.eps, nlo, nhi);
+  const float* G = static_cast<const float*>(J.n_gas);
+  const float d = __double2float_rn(dne);
+  static_cast<float*>(J.dne)[c] = G ? d * G[c] : d;
+  J.lo[c] = (uint8_t)nlo;
+  J.hi[c] = (uint8_t)nhi;
+}
+
+__global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ StagedF32 tabs[kMaxJobs];
+  for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
+  __syncthreads();
+  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrFallback]);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
+    const int c = (int)a.ws.queue[i];
+    const int jid = a.ws.queue_job[i];
+    const JobIO& J = a.job[jid];
+    const StagedF32& tab = tabs[jid];
+    const int lo = J.lo[c], hi = J.hi[c];
+    switch (hi - lo + 1) {
+      case 2:
+        fb_cell<2>(J, a.pol, tab, c, lo, hi);
+        break;
+      case 3:
+        fb_cell<3>(J, a.pol, tab, c, lo, hi);
+        break;
+      case 4:
+        fb_cell<4>(J, a.pol, tab, c, lo, hi);
+        break;
+      case 5:
+        fb_cell<5>(J, a.pol, tab, c, lo, hi);
+        break;
+      case 6:
+        fb_cell<6>(J, a.pol, tab, c, lo, hi);
+        break;
+      default:
+        break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// One instantiation of the streaming kernel: its function and smem needs.
+struct StreamVariant {
+  const void* fn;
+  int Q, W;
+  size_t (*smem)(int);
+};
+
+template <int Q, int W>
+size_t smem_of(int njobs) {
+  return stream_smem<Q, W>(njobs);
+}
+
+#define ION_VARIANT(Q, W) \
+  { reinterpret_cast<const void*>(&ion_stream_kernel<Q, W>), Q, W, &smem_of<Q, W> }
+const StreamVariant kVariants[] = {ION_VARIANT(1, 2), ION_VARIANT(1, 4), ION_VARIANT(1, 8),
+                                   ION_VARIANT(2, 2), ION_VARIANT(2, 4), ION_VARIANT(2, 8),
+                                   ION_VARIANT(4, 2), ION_VARIANT(4, 4), ION_VARIANT(4, 8)};
+#undef ION_VARIANT
+
+const StreamVariant* find_variant(int Q, int W) {
+  for (const auto& v : kVariants)
+    if (v.Q == Q && v.W == W) return &v;
+  return nullptr;
+}
+
+}  // namespace
+
+LaunchShape default_shape() { return {4, 4, 0}; }
+
+bool valid_shape(const LaunchShape& s) {
+  return find_variant(s.cells_per_lane, s.warps_per_block) != nullptr &&
+         s.blocks_per_sm >= 0 && s.blocks_per_sm <= 32;
+}
+
+size_t step_workspace_bytes(int64_t ncells, bool f64) {
+  if (f64) return kHdrBytes;
+  const size_t n = (size_t)ncells;
+  return kHdrBytes + round256(4 * n) + round256(n) + round256(4 * n) + round256(n) +
+         round256(4 * n) + round256(2 * n) + round256(4 * n * ION_MAX_WINDOW);
+}
+
+void bind_workspace(Scratch& s, void* ws, int64_t ncells) {
+  char* p = static_cast<char*>(ws);
+  const size_t n = (size_t)ncells;
+  s.hdr = reinterpret_cast<uint32_t*>(p);
+  p += kHdrBytes;
+  s.queue = reinterpret_cast<uint32_t*>(p);
+  p += round256(4 * n);
+  s.queue_job = reinterpret_cast<uint8_t*>(p);
+  p += round256(n);
+  s.rec_c = reinterpret_cast<uint32_t*>(p);
+  p += round256(4 * n);
+  s.rec_job = reinterpret_cast<uint8_t*>(p);
+  p += round256(n);
+  s.rec_E = reinterpret_cast<float*>(p);
+  p += round256(4 * n);
+  s.rec_lohi = reinterpret_cast<uint16_t*>(p);
+  p += round256(2 * n);
+  s.rec_V = reinterpret_cast<float*>(p);
+  s.rec_cap = (int64_t)n;
+}
+
+cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms,
+                             cudaStream_t s) {
+  const StreamVariant* v = find_variant(shape.cells_per_lane, shape.warps_per_block);
+  if (!v) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(a.ws.hdr, 0, kHdrWords * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const int chunk = 32 * v->Q;
+  int total = 0, cells = 0;
+  for (int j = 0; j < a.njobs; ++j) {
+    a.job[j].chunk0 = total;
+    total += a.job[j].ncells / chunk;
+    cells += a.job[j].ncells;
+  }
+  a.nchunks = total;
+  if (cells == 0) return cudaSuccess;
+  const size_t smem = v->smem(a.njobs);
+  if ((e = cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem)) != cudaSuccess)
+    return e;
+  int fit = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, v->fn, v->W * 32, smem)) !=
+      cudaSuccess)
+    return e;
+  if (fit < 1) return cudaErrorInvalidConfiguration;
+  const int per_sm = shape.blocks_per_sm > 0 && shape.blocks_per_sm < fit ? shape.blocks_per_sm
+                                                                          : fit;
+  const int64_t need = ((int64_t)total + v->W - 1) / v->W;
+  int blocks = (int)(need < (int64_t)per_sm * num_sms ? need : (int64_t)per_sm * num_sms);
+  if (blocks < 1) blocks = 1;  // the tails still need a warp
+  void* args[] = {&a};
+  if ((e = cudaLaunchKernel(v->fn, blocks, v->W * 32, args, smem, s)) != cudaSuccess) return e;
+  ion_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const bool need_fb = (a.pol.flags & ION_NO_FP64_FALLBACK) == 0 &&
+                       ((a.pol.flags & ION_FORCE_FP64_COEF) != 0 || a.pol.gap > 0.0);
+  if (need_fb) {
+    ion_fb_kernel<<<2 * num_sms, 128, 0, s>>>(a);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace ion

@@ -35,8 +35,13 @@ ION_MAX_WINDOW = 6
 
 #: every symbol include/ionize.h declares
 EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
-           "ion_rates", "ion_step_workspace_bytes", "ion_step", "ion_step_noalloc",
-           "ion_last_error")
+           "ion_rates", "ion_step_workspace_bytes", "ion_step",
+           "ion_step_batched_workspace_bytes", "ion_step_batched", "ion_autotune",
+           "ion_step_noalloc", "ion_last_error")
+
+ION_MAX_JOBS = 8
+#: launch shapes the library is built with (cells per lane, warps per block)
+LAUNCH_SHAPES = [(q, w) for q in (1, 2, 4) for w in (2, 4, 8)]
 
 #: largest ncells of one ion_step_noalloc call
 ION_STEP_NOALLOC_MAX_CELLS = 262144
@@ -58,6 +63,21 @@ class _Constants(ctypes.Structure):
 
 class _StepOpts(ctypes.Structure):
     _fields_ = [("eps_shift", ctypes.c_double), ("degen_gap", ctypes.c_double)]
+
+
+class _BatchJob(ctypes.Structure):
+    _fields_ = [("species", ctypes.c_void_p), ("E", ctypes.c_void_p), ("N", ctypes.c_void_p),
+                ("ld", ctypes.c_int64), ("ncells", ctypes.c_int64), ("k_lo", ctypes.c_void_p),
+                ("k_hi", ctypes.c_void_p), ("dne", ctypes.c_void_p), ("n_gas", ctypes.c_void_p)]
+
+
+class LaunchShape(ctypes.Structure):
+    _fields_ = [("cells_per_lane", ctypes.c_int), ("warps_per_block", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int)]
+
+    def __repr__(self):
+        return (f"LaunchShape(cells_per_lane={self.cells_per_lane}, "
+                f"warps_per_block={self.warps_per_block}, blocks_per_sm={self.blocks_per_sm})")
 
 
 _vp = ctypes.c_void_p
@@ -85,6 +105,18 @@ def _declare(lib):
     lib.ion_step.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                              _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp,
                              ctypes.c_size_t, _vp]
+    lib.ion_step_batched_workspace_bytes.restype = ctypes.c_size_t
+    lib.ion_step_batched_workspace_bytes.argtypes = [ctypes.POINTER(_BatchJob), ctypes.c_int,
+                                                     ctypes.c_int]
+    lib.ion_step_batched.restype = ctypes.c_int
+    lib.ion_step_batched.argtypes = [ctypes.POINTER(_BatchJob), ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(_StepOpts), ctypes.c_int,
+                                     ctypes.POINTER(LaunchShape), _vp, ctypes.c_size_t, _vp]
+    lib.ion_autotune.restype = ctypes.c_int
+    lib.ion_autotune.argtypes = [ctypes.POINTER(_BatchJob), ctypes.c_int, ctypes.c_double,
+                                 ctypes.POINTER(_StepOpts), ctypes.c_int, _vp, ctypes.c_size_t,
+                                 ctypes.c_int, _vp, ctypes.POINTER(LaunchShape),
+                                 ctypes.POINTER(ctypes.c_float)]
     lib.ion_step_noalloc.restype = ctypes.c_int
     lib.ion_step_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                      _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp]
@@ -259,6 +291,68 @@ def step_noalloc(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tens
     _check(lib().ion_step_noalloc(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
                                   _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
                                   ctypes.byref(opts), int(flags), _stream(E)))
+
+
+def _jobs(jobs, f64=False):
+    """jobs: sequence of (Species, E, N, k_lo, k_hi, dne[, n_gas])."""
+    if not 1 <= len(jobs) <= ION_MAX_JOBS:
+        raise ValueError(f"1..{ION_MAX_JOBS} jobs")
+    dt_ = torch.float64 if f64 else torch.float32
+    arr = (_BatchJob * len(jobs))()
+    dev = None
+    for i, jb in enumerate(jobs):
+        sp, E, N, lo, hi, dne = jb[:6]
+        ng = jb[6] if len(jb) > 6 else None
+        _need(E, "E", dt_)
+        dev = dev or E.device
+        for t, nm in ((N, "N"), (dne, "dne")):
+            _need(t, nm, dt_, dev)
+        _need(lo, "k_lo", torch.uint8, dev)
+        _need(hi, "k_hi", torch.uint8, dev)
+        if ng is not None:
+            _need(ng, "n_gas", dt_, dev)
+        if N.dim() != 2 or N.shape[0] != sp.Z + 1:
+            raise ValueError(f"job {i}: N must have shape (Z+1, ld)")
+        arr[i] = _BatchJob(sp.handle.value, E.data_ptr(), N.data_ptr(), N.shape[1], E.numel(),
+                           lo.data_ptr(), hi.data_ptr(), dne.data_ptr(),
+                           ng.data_ptr() if ng is not None else None)
+    return arr, dev
+
+
+def batched_workspace(jobs, flags: int = ION_F32, device=None) -> torch.Tensor:
+    n = sum(jb[1].numel() for jb in jobs)
+    return workspace(n, flags, device or jobs[0][1].device)
+
+
+def step_batched(jobs, dt: float, ws: torch.Tensor | None = None, eps_shift: float = 1e-6,
+                 degen_gap: float = 1e-3, flags: int = ION_F32,
+                 shape: LaunchShape | tuple | None = None) -> torch.Tensor:
+    """ion_step_batched over jobs = [(Species, E, N, k_lo, k_hi, dne[, n_gas]), ...]."""
+    arr, dev = _jobs(jobs, bool(flags & ION_F64_PLAIN))
+    if ws is None:
+        ws = batched_workspace(jobs, flags, dev)
+    if shape is not None and not isinstance(shape, LaunchShape):
+        shape = LaunchShape(*shape)
+    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    _check(lib().ion_step_batched(arr, len(jobs), float(dt), ctypes.byref(opts), int(flags),
+                                  ctypes.byref(shape) if shape is not None else None,
+                                  _ptr(ws), ws.numel(), _stream(jobs[0][1])))
+    return ws
+
+
+def autotune(jobs, dt: float, ws: torch.Tensor | None = None, reps: int = 3,
+             eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32):
+    """ion_autotune: (best LaunchShape, its median ms).  Steps the jobs' arrays."""
+    arr, dev = _jobs(jobs)
+    if ws is None:
+        ws = batched_workspace(jobs, flags, dev)
+    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    best = LaunchShape()
+    ms = ctypes.c_float()
+    _check(lib().ion_autotune(arr, len(jobs), float(dt), ctypes.byref(opts), int(flags),
+                              _ptr(ws), ws.numel(), int(reps), _stream(jobs[0][1]),
+                              ctypes.byref(best), ctypes.byref(ms)))
+    return best, float(ms.value)
 
 
 def counters(ws: torch.Tensor):

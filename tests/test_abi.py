@@ -60,8 +60,8 @@ def test_host_side_rejections():
 
 def test_workspace_sizes():
     assert ionize.workspace_bytes(0) == 256
-    # header + FP64 queue (4 B/cell) + stiff records (34 B/cell), each section
-    # 256-byte aligned
+    # header + FP64 queue (5 B/cell) + stiff records (35 B/cell), each of the
+    # seven sections 256-byte aligned
     for n in (1, 31, 32, 1000, 33554432):
-        assert 256 + 38 * n <= ionize.workspace_bytes(n) <= 256 + 38 * n + 5 * 256
+        assert 256 + 40 * n <= ionize.workspace_bytes(n) <= 256 + 40 * n + 7 * 256
     assert ionize.workspace_bytes(1000, ionize.ION_F64_PLAIN) == 256
