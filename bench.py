@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -299,6 +300,66 @@ def main():
     diff_32_64 = float((N[:, :n].double() - N64[:, :n]).abs().max())
     del E64, N64_0, N64, dne64
 
+    # -- batched form: N (20M), Ar-like (8M), Kr-like (2M) cells in one launch -
+    batched = None
+    if not args.no_batched:
+        bjobs_wl = W.mixed_batch(scale=1.0, seed=3, device=dev)
+        bsp = [ionize.Species(w_.species.U, w_.species.l, w_.species.m) for w_ in bjobs_wl]
+        pristine = [(w_.N.clone(), w_.lo.clone(), w_.hi.clone()) for w_ in bjobs_wl]
+        bdne = [torch.empty(w_.ncells, device=dev) for w_ in bjobs_wl]
+        bjobs = [(sp_, w_.E, w_.N, w_.lo, w_.hi, d_) for sp_, w_, d_ in zip(bsp, bjobs_wl, bdne)]
+        bws = ionize.batched_workspace(bjobs)
+
+        def brestore():
+            for w_, (n0, l0, h0) in zip(bjobs_wl, pristine):
+                w_.N.copy_(n0)
+                w_.lo.copy_(l0)
+                w_.hi.copy_(h0)
+            flush.zero_()
+
+        # the autotuner steps the arrays; restore afterwards
+        shape, tune_ms = ionize.autotune(bjobs, 0.05, ws=bws, reps=3)
+        bt = []
+        for s_ in range(3 + max(5, args.steps // 5)):
+            brestore()
+            a_ = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            ionize.step_batched(bjobs, 0.05, ws=bws, shape=shape)
+            b_.record(stream)
+            if s_ >= 3:
+                bt.append((a_, b_))
+        torch.cuda.synchronize()
+        bms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in bt]))
+        bcells = sum(w_.ncells for w_ in bjobs_wl)
+        bbytes = sum(int(W.window_bytes_per_cell(l0, h0).sum()) for (_, l0, h0) in pristine)
+        # accuracy on sampled cells of each species
+        bacc = 0.0
+        if rank == 0:
+            import oracle
+            brestore()
+            samples = []
+            for w_ in bjobs_wl:
+                ix = torch.tensor(sample_indices(w_.ncells, 2000, 5), device=dev)
+                samples.append((ix, w_.E[ix].double().cpu().numpy(),
+                                w_.N[:, ix].double().cpu().numpy(), w_.lo[ix].cpu().numpy(),
+                                w_.hi[ix].cpu().numpy()))
+            ionize.step_batched(bjobs, 0.05, ws=bws, shape=shape)
+            torch.cuda.synchronize()
+            for w_, (ix, Es_, Ns_, ls_, hs_) in zip(bjobs_wl, samples):
+                osp_ = oracle.Species(w_.species.U, w_.species.l, w_.species.m)
+                No_, _, _, _ = oracle.step(osp_, Es_, Ns_, 0.05, ls_, hs_)
+                bacc = max(bacc, float(np.abs(w_.N[:, ix].double().cpu().numpy() - No_).max()))
+        batched = {"value": bcells / (bms * 1e-3), "ms_per_step": bms, "cells": bcells,
+                   "species": "N 20M + Ar-like 8M + Kr-like 2M",
+                   "achieved_GBs": bbytes / (bms * 1e-3) / 1e9,
+                   "frac_of_hbm_peak": bbytes / (bms * 1e-3) / 1e9 / peaks()[0],
+                   "launch_shape": {"cells_per_lane": shape.cells_per_lane,
+                                    "warps_per_block": shape.warps_per_block,
+                                    "blocks_per_sm": shape.blocks_per_sm},
+                   "max_abs_err_N_vs_oracle": bacc}
+        del bjobs, bjobs_wl, pristine, bws
+
     # -- end to end through host buffers -------------------------------------
     e2e = None
     if not args.no_e2e:
@@ -389,6 +450,7 @@ def main():
                                   "second_kernel_cells": stiff},
             "fp64_plain": {"value": n / (ms64 * 1e-3), "ms_per_step": ms64,
                            "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9},
+            "batched_mixed_species": batched,
         },
         "accuracy": acc,
         "gpu_launches": 3 * args.steps,
