@@ -121,7 +121,7 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
  * a 256-byte header plus, for ION_F32, 40 bytes per cell: a 5-byte queue
  * slot (cells whose Bateman coefficients are computed in FP64) and a 35-byte
- * record (cells with a rate W dt > 0.025, finished by a second kernel from
+ * record (cells with a rate W dt > 1, finished by a second kernel from
  * the inputs the first one loaded). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
 
@@ -161,7 +161,7 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *          whose coefficients were computed in FP64, word 1 the cells left
  *          untouched because their window was invalid (lo > hi, hi > Z or
  *          w > ION_MAX_WINDOW), word 2 the cells that had a rate with
- *          W dt > 0.025 (finished on the long path).
+ *          W dt > 1 (finished by the second kernel in the Bateman form).
  * Alignment: E, N, dne, n_gas aligned to their element size; with ION_F32
  * k_lo and k_hi 4-byte aligned (they are copied four cells at a time).
  * Calls that share a workspace must not overlap on the device.

@@ -8,9 +8,9 @@
 //       ahead and each lane's own window planes one chunk ahead (one copy of
 //       4*Q bytes per plane when the lane's cells share their window), so the
 //       loads in flight cost no registers and the traffic is exactly the
-//       cells' windows.  A cell whose rates all have W dt <= 0.025 is
-//       finished here (at most four Taylor terms of exp(dt A)).  The others
-//       ("stiff" cells) write the inputs already loaded into a record queue:
+//       cells' windows.  A cell whose rates all have W dt <= 1 is finished
+//       here with the Taylor series of exp(dt A).  The others ("stiff" cells,
+//       the Bateman form) write the inputs already loaded into a record queue:
 //       in a laser field |E| swings from zero to its peak every few cells, so
 //       most warps near the pulse hold a few stiff cells, and finishing them
 //       in place would make every such warp run the longest path of its
@@ -34,8 +34,12 @@ namespace ion {
 namespace {
 
 constexpr int kStages = 3;
-constexpr float kLamEasy = 0.025f;  // 2 kLamEasy <= kThrF32[4]: 4 terms
-constexpr int kEasyTerms = 4;
+// The streaming kernel finishes every cell whose rates all have
+// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[16].
+constexpr float kLamEasy = 1.0f;
+constexpr int kEasyTerms = 16;
+// Rates with W dt above this are recomputed in float-float arithmetic.
+constexpr float kLamPrecise = 1.0f / 64.0f;
 
 template <int Q>
 struct VecOf;
@@ -124,12 +128,12 @@ __device__ __forceinline__ void append_record(const Scratch& S, bool take, int j
 // Easy path of the lane's Q cells (c0..c0+Q-1 of job J, window bound WM).
 // Every lane of the warp calls this.  Cells whose rates all have
 // W dt <= kLamEasy are finished; stiff[j] marks the others, left untouched.
-// Every window rate takes the plain FP32 exponent y = (a_hi + a_lo) -
+// Every window rate first takes the plain FP32 exponent y = (a_hi + a_lo) -
 // b log2|E| - C/|E|: its error is below ~6e-5 in log2 units even for terms of
 // 10^3, i.e. a relative error of W dt below 4e-5, which moves populations by
-// at most 0.025 * 4e-5 = 1e-6 in the cells this path finishes (the stiff
-// path recomputes its rates in float-float).  The Taylor series runs the
-// warp's largest term count (extra terms only add accuracy).
+// at most 4e-5 W dt; rates above kLamPrecise = 2^-6 (where that could reach
+// 6e-7) are recomputed in float-float.  The Taylor series runs the warp's
+// largest term count (extra terms only add accuracy).
 template <int Q, int WM>
 __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
                                            const StagedF32& tab, const QStage<Q>& st,
@@ -164,15 +168,15 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
       const bool on = live && r < w[j] - 1 && q <= (float)kCutoffLog2;
       lam[j][r] = on ? ex2_approx(fminf(y, 99.0f)) : 0.0f;
     }
+#pragma unroll
+    for (int r = 0; r < WM - 1; ++r)
+      if (lam[j][r] > kLamPrecise) lam[j][r] = rate_dt_f32(tab, base + r, f);
     float lmax = 0.0f;
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
     stiff[j] = lmax > kLamEasy;
     const float x = stiff[j] ? 0.0f : 2.0f * lmax;
-    int R = 0;
-#pragma unroll
-    for (int i = 0; i < kEasyTerms; ++i) R += x > kThrF32[i] ? 1 : 0;
-    Rl = max(Rl, R);
+    Rl = max(Rl, DDParams<float>::terms(x, kEasyTerms));
   }
   const int Rw = __reduce_max_sync(kFull, Rl);
   float dne[Q];
@@ -189,10 +193,9 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
       t[i] = i < w[j] ? v[j][i] : 0.0f;
       inc[i] = 0.0f;
     }
-#pragma unroll
-    for (int k = 1; k <= kEasyTerms; ++k) {
-      if (k > Rw) break;
-      const float rk = 1.0f / k;
+#pragma unroll 1
+    for (int k = 1; k <= Rw; ++k) {
+      const float rk = 1.0f / (float)k;
 #pragma unroll
       for (int i = WM - 1; i >= 0; --i) {
         const float gain = i > 0 ? lam[j][i - 1] * t[i - 1] : 0.0f;
