@@ -35,9 +35,13 @@ namespace {
 
 constexpr int kStages = 3;
 // The streaming kernel finishes every cell whose rates all have
-// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[16].
-constexpr float kLamEasy = 1.0f;
-constexpr int kEasyTerms = 16;
+// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[9].
+constexpr float kLamEasy = 0.25f;
+constexpr int kEasyTerms = 9;
+// 1/k! for the Taylor terms of the streaming kernel
+__device__ constexpr float kInvFactF32[kEasyTerms + 1] = {
+    1.0f,          1.0f,           1.0f / 2,        1.0f / 6,        1.0f / 24,
+    1.0f / 120,    1.0f / 720,     1.0f / 5040,     1.0f / 40320,    1.0f / 362880};
 // Rates with W dt above this are recomputed in float-float arithmetic.
 constexpr float kLamPrecise = 1.0f / 64.0f;
 
@@ -187,20 +191,21 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     nlo[j] = lo[j];
     nhi[j] = hi[j];
     if (stiff[j] || w[j] < 2) continue;
-    float t[WM], inc[WM];
+    // u = (dt A)^k v unnormalized (|dt A| <= 2 kLamEasy keeps it small);
+    // inc = sum_k u / k!
+    float u[WM], inc[WM];
 #pragma unroll
     for (int i = 0; i < WM; ++i) {
-      t[i] = i < w[j] ? v[j][i] : 0.0f;
+      u[i] = i < w[j] ? v[j][i] : 0.0f;
       inc[i] = 0.0f;
     }
 #pragma unroll 1
     for (int k = 1; k <= Rw; ++k) {
-      const float rk = 1.0f / (float)k;
+      const float ck = kInvFactF32[k];
 #pragma unroll
       for (int i = WM - 1; i >= 0; --i) {
-        const float gain = i > 0 ? lam[j][i - 1] * t[i - 1] : 0.0f;
-        t[i] = (gain - lam[j][i] * t[i]) * rk;
-        inc[i] += t[i];
+        u[i] = fmaf(-lam[j][i], u[i], i > 0 ? lam[j][i - 1] * u[i - 1] : 0.0f);
+        inc[i] = fmaf(u[i], ck, inc[i]);
       }
     }
     float cum = 0.0f;
