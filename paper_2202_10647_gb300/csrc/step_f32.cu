@@ -35,28 +35,13 @@ namespace {
 
 constexpr int kStages = 3;
 // The streaming kernel finishes every cell whose rates all have
-// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[16].
-constexpr float kLamEasy = 1.0f;
-constexpr int kEasyTerms = 16;
+// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[9].
+constexpr float kLamEasy = 0.25f;
+constexpr int kEasyTerms = 9;
 // 1/k! for the Taylor terms of the streaming kernel
 __device__ constexpr float kInvFactF32[kEasyTerms + 1] = {
-    1.0f,
-    1.0f,
-    1.0f / 2,
-    1.0f / 6,
-    1.0f / 24,
-    1.0f / 120,
-    1.0f / 720,
-    1.0f / 5040,
-    1.0f / 40320,
-    1.0f / 362880,
-    1.0f / 3628800,
-    1.0f / 39916800,
-    1.0f / 479001600,
-    1.0f / 6227020800.0f,
-    1.0f / 87178291200.0f,
-    1.0f / 1307674368000.0f,
-    1.0f / 20922789888000.0f};
+    1.0f,          1.0f,           1.0f / 2,        1.0f / 6,        1.0f / 24,
+    1.0f / 120,    1.0f / 720,     1.0f / 5040,     1.0f / 40320,    1.0f / 362880};
 // Rates with W dt above this are recomputed in float-float arithmetic.
 constexpr float kLamPrecise = 1.0f / 64.0f;
 
@@ -129,7 +114,7 @@ __device__ __forceinline__ void append_record(const Scratch& S, bool take, int j
   if (!m) return;
   const int lane = threadIdx.x & 31;
   unsigned base = 0;
-  if (lane == 0) base = atomicAdd(&S.hdr[kHdrRecords], (unsigned)__popc(m));
+  if (lane == 0) base = atomicAdd(&S.hdr[kHdrStiff], (unsigned)__popc(m));
   base = __shfl_sync(kFull, base, 0);
   if (take) {
     const unsigned i = base + __popc(m & ((1u << lane) - 1u));
@@ -283,19 +268,6 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
   }
 }
 
-// A stiff cell of a staged chunk (lane's cell j): the full path of
-// finish_cell from the staged window, window bound WM.
-template <int Q, int WM>
-__device__ __forceinline__ bool staged_stiff(const JobIO& J, const Policy& pol,
-                                             const StagedF32& tab, const QStage<Q>& st,
-                                             int lane, int j, int c, float Ec, int lo,
-                                             int hi) {
-  float v[WM];
-#pragma unroll
-  for (int r = 0; r < WM; ++r) v[r] = r < hi - lo + 1 ? vget(st.P[r][lane], j) : 0.0f;
-  return finish_cell<F32Form, WM>(J, pol, tab, c, Ec, lo, hi, v, true);
-}
-
 template <int Q>
 constexpr size_t stage_bytes() {
   return sizeof(QStage<Q>);
@@ -398,7 +370,6 @@ __global__ void __launch_bounds__(W * 32)
 
   // chunk k lives in stage s0, k+1 in s1, k+2 in s2
   int s0 = 0, s1 = 1, s2 = 2;
-  unsigned nstiff = 0;  // stiff cells this warp finished (statistics)
   issue_front(0, s0);
   issue_front(1, s1);
   cp_async_wait<1>();  // front(0)
@@ -467,26 +438,17 @@ __global__ void __launch_bounds__(W * 32)
     } else {
       easy_cells<Q, 6>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
     }
-    // stiff cells (a rate with W dt > kLamEasy): the Bateman form here, from
-    // the staged inputs, with the warp's window bucket
+    // stiff cells: their inputs (as loaded) go to the record queue
     bool any = false;
 #pragma unroll
     for (int j = 0; j < Q; ++j) any = any || stiff[j];
     if (__ballot_sync(kFull, any)) {
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
-        bool fb = false;
-        if (stiff[j]) {
-          if (WMw <= 2)
-            fb = staged_stiff<Q, 2>(J, a.pol, tab, st, lane, j, c0 + j, Ev[j], lo[j], hi[j]);
-          else if (WMw <= 4)
-            fb = staged_stiff<Q, 4>(J, a.pol, tab, st, lane, j, c0 + j, Ev[j], lo[j], hi[j]);
-          else
-            fb = staged_stiff<Q, 6>(J, a.pol, tab, st, lane, j, c0 + j, Ev[j], lo[j], hi[j]);
-        }
-        warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb,
-                    (uint32_t)(c0 + j), (uint8_t)jid);
-        nstiff += __popc(__ballot_sync(kFull, stiff[j]));
+        float vin[ION_MAX_WINDOW];
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = vget(st.P[r][lane], j);
+        append_record(a.ws, stiff[j], jid, c0 + j, Ev[j], lo[j], hi[j], vin);
       }
     }
     __syncwarp();
@@ -496,7 +458,6 @@ __global__ void __launch_bounds__(W * 32)
     s2 = t;
   }
   cp_async_wait<0>();
-  if (lane == 0 && nstiff) atomicAdd(&a.ws.hdr[kHdrStiff], nstiff);
 
   // each job's last, partial chunk (ncells % (32 Q) cells): every valid cell
   // becomes a record for the stiff kernel, which runs the full path
@@ -545,7 +506,7 @@ __global__ void __launch_bounds__(256)
   __shared__ StagedF32 tabs[kMaxJobs];
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   __syncthreads();
-  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrRecords]);
+  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrStiff]);
   const unsigned stride = gridDim.x * blockDim.x;
   const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
