@@ -35,13 +35,28 @@ namespace {
 
 constexpr int kStages = 3;
 // The streaming kernel finishes every cell whose rates all have
-// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[9].
-constexpr float kLamEasy = 0.25f;
-constexpr int kEasyTerms = 9;
+// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[16].
+constexpr float kLamEasy = 1.0f;
+constexpr int kEasyTerms = 16;
 // 1/k! for the Taylor terms of the streaming kernel
 __device__ constexpr float kInvFactF32[kEasyTerms + 1] = {
-    1.0f,          1.0f,           1.0f / 2,        1.0f / 6,        1.0f / 24,
-    1.0f / 120,    1.0f / 720,     1.0f / 5040,     1.0f / 40320,    1.0f / 362880};
+    1.0f,
+    1.0f,
+    1.0f / 2,
+    1.0f / 6,
+    1.0f / 24,
+    1.0f / 120,
+    1.0f / 720,
+    1.0f / 5040,
+    1.0f / 40320,
+    1.0f / 362880,
+    1.0f / 3628800,
+    1.0f / 39916800,
+    1.0f / 479001600,
+    1.0f / 6227020800.0f,
+    1.0f / 87178291200.0f,
+    1.0f / 1307674368000.0f,
+    1.0f / 20922789888000.0f};
 // Rates with W dt above this are recomputed in float-float arithmetic.
 constexpr float kLamPrecise = 1.0f / 64.0f;
 
