@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-krypton", action="store_true")
     return ap.parse_args()
 
 
@@ -360,6 +361,58 @@ def main():
                    "max_abs_err_N_vs_oracle": bacc}
         del bjobs, bjobs_wl, pristine, bws
 
+    # -- Kr-like 512x512x256 cells, 50 steps captured in one CUDA graph -------
+    krypton = None
+    if not args.no_krypton:
+        from paper_2202_10647_gb300 import multistep
+        kgrid = (256, 512, 512)
+        kn = kgrid[0] * kgrid[1] * kgrid[2]
+        A_, B_ = W.krypton_beam_terms(*kgrid, device=dev)
+        S_ = W.krypton_scale(A_)
+        kfields = [W.krypton_field(A_, B_, s_ * 0.05, S_) for s_ in range(50)]
+        del A_, B_
+        kwl = W.krypton_initial(kn, device=dev)
+        ksp = ionize.Species(kwl.species.U, kwl.species.l, kwl.species.m)
+        kdne = torch.empty(kn, device=dev)
+        kws = ionize.workspace(kn)
+        graphs = {name: multistep.StepGraph(ksp, kfields, kwl.N, kwl.lo, kwl.hi, kdne, 0.05,
+                                            ws=kws, conservation=chk)
+                  for name, chk in (("with_check", True), ("steps_only", False))}
+
+        def kreset():
+            kwl.N.zero_()
+            kwl.N[0, :kn] = 1.0
+            kwl.lo.zero_()
+            kwl.hi.fill_(3)
+
+        kres = {}
+        for name, g_ in graphs.items():
+            ts_ = []
+            for r_ in range(4):
+                kreset()
+                a_ = torch.cuda.Event(enable_timing=True)
+                b_ = torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                g_.replay()
+                b_.record(stream)
+                torch.cuda.synchronize()
+                if r_ >= 1:
+                    ts_.append(a_.elapsed_time(b_))
+            kres[name] = float(np.median(ts_))
+        cons = graphs["with_check"].cons.cpu().numpy()
+        krypton = {"value": 50 * kn / (kres["with_check"] * 1e-3),
+                   "ms_per_50_steps": kres["with_check"],
+                   "value_steps_only": 50 * kn / (kres["steps_only"] * 1e-3),
+                   "ms_per_50_steps_steps_only": kres["steps_only"],
+                   "cells": kn, "grid": list(kgrid), "species": "Kr-like (Z=36), 37 planes",
+                   "field": "16 seeded Gaussian beams, lambda 0.8 um, 6000 GV/m peak at t=0",
+                   "graph": "50 x (ion_step + ion_conservation) in one CUDA graph",
+                   "max_abs_sum_N_minus_1": {"after_step_1": float(cons[0]),
+                                             "after_step_50": float(cons[-1]),
+                                             "max": float(cons.max())},
+                   "windows_slid_fraction": float((kwl.lo > 0).double().mean())}
+        del graphs, kfields, kwl, kws, kdne
+
     # -- end to end through host buffers -------------------------------------
     e2e = None
     if not args.no_e2e:
@@ -441,7 +494,7 @@ def main():
                    "form": "FP32 + FP64 coefficients for |W_i-W_j| < 1e-3 max(W_i,W_j)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "ion_step (ion_step_f32_kernel + ion_step_f32_hard_kernel + ion_step_fb_kernel)",
+                     "kernel": "ion_step (ion_stream_kernel + ion_stiff_kernel + ion_fb_kernel)",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": main_ms},
         "forms": {
@@ -451,6 +504,7 @@ def main():
             "fp64_plain": {"value": n / (ms64 * 1e-3), "ms_per_step": ms64,
                            "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9},
             "batched_mixed_species": batched,
+            "krypton_beams_50_steps_graph": krypton,
         },
         "accuracy": acc,
         "gpu_launches": 3 * args.steps,

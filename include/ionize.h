@@ -259,6 +259,24 @@ ION_API int ion_step_noalloc(const ion_species* sp, const void* E, void* N,
                              const void* n_gas, const ion_step_opts* opts,
                              int flags, void* stream);
 
+/* ion_conservation -- the conservation diagnostic of multi-step runs.  The
+ * update of Eqs. 4-9 moves population between the states of a window and
+ * leaves the other states alone, so sum_k N_k of a cell never changes; this
+ * call measures how well a run keeps it.
+ *   N        device SoA, plane k of cell c at N[k*ld + c], float
+ *            (ION_DTYPE_F32) or double (ION_DTYPE_F64).
+ *   ld, ncells  as in ion_step; 0 <= ncells <= ld (0 is a no-op).
+ *   nplanes  planes summed per cell, 1..ION_MAX_Z+1 (Z+1 for a species).
+ *   target   the expected sum (1 for normalized populations).
+ *   out_max  device float, 4-byte aligned: receives
+ *            max_c |sum_{k<nplanes} N[k*ld+c] - target| (0 when ncells is
+ *            0), the sums taken in double; a NaN sum gives NaN.
+ * Enqueues a 4-byte memset of *out_max and one kernel that reads
+ * nplanes*ncells elements (graph-capturable).
+ * Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_conservation(const void* N, int64_t ld, int64_t ncells, int nplanes,
+                             double target, int dtype, float* out_max, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 ION_API const char* ion_last_error(void);
 

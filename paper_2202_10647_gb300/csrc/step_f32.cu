@@ -25,6 +25,7 @@
 //
 // One step is Eqs. 1-9 of the paper per cell; see ion_device.cuh.
 #include <cstdint>
+#include <mutex>
 
 #include "ion_cell.cuh"
 #include "ion_step.cuh"
@@ -656,6 +657,37 @@ const StreamVariant* find_variant(int Q, int W) {
   return nullptr;
 }
 
+// Resident blocks per SM of a variant with `njobs` staged tables, set up and
+// measured once per (device, variant, njobs): later calls (and calls made
+// while a stream is being captured) only read the cache.
+constexpr int kMaxDevices = 64;
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+std::mutex g_fit_mu;
+int g_fit[kMaxDevices][kNumVariants][kMaxJobs + 1];  // 0: not measured yet
+
+cudaError_t resident_blocks(const StreamVariant& v, int njobs, size_t smem, int* fit) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int vi = (int)(&v - kVariants);
+  const bool cache = dev >= 0 && dev < kMaxDevices;
+  std::lock_guard<std::mutex> lock(g_fit_mu);
+  if (cache && g_fit[dev][vi][njobs] > 0) {
+    *fit = g_fit[dev][vi][njobs];
+    return cudaSuccess;
+  }
+  // the opt-in limit covers every job count, so no later call lowers it
+  // under a launch that needs more
+  if ((e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)v.smem(kMaxJobs))) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, v.fn, v.W * 32, smem)) !=
+      cudaSuccess)
+    return e;
+  if (cache && *fit > 0) g_fit[dev][vi][njobs] = *fit;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 LaunchShape default_shape() { return {4, 4, 0}; }
@@ -709,13 +741,8 @@ cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms
   a.nchunks = total;
   if (cells == 0) return cudaSuccess;
   const size_t smem = v->smem(a.njobs);
-  if ((e = cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem)) != cudaSuccess)
-    return e;
   int fit = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, v->fn, v->W * 32, smem)) !=
-      cudaSuccess)
-    return e;
+  if ((e = resident_blocks(*v, a.njobs, smem, &fit)) != cudaSuccess) return e;
   if (fit < 1) return cudaErrorInvalidConfiguration;
   const int per_sm = shape.blocks_per_sm > 0 && shape.blocks_per_sm < fit ? shape.blocks_per_sm
                                                                           : fit;

@@ -37,7 +37,7 @@ ION_MAX_WINDOW = 6
 EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_rates", "ion_step_workspace_bytes", "ion_step",
            "ion_step_batched_workspace_bytes", "ion_step_batched", "ion_autotune",
-           "ion_step_noalloc", "ion_last_error")
+           "ion_step_noalloc", "ion_conservation", "ion_last_error")
 
 ION_MAX_JOBS = 8
 #: launch shapes the library is built with (cells per lane, warps per block)
@@ -117,6 +117,9 @@ def _declare(lib):
                                  ctypes.POINTER(_StepOpts), ctypes.c_int, _vp, ctypes.c_size_t,
                                  ctypes.c_int, _vp, ctypes.POINTER(LaunchShape),
                                  ctypes.POINTER(ctypes.c_float)]
+    lib.ion_conservation.restype = ctypes.c_int
+    lib.ion_conservation.argtypes = [_vp, _i64, _i64, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, _vp, _vp]
     lib.ion_step_noalloc.restype = ctypes.c_int
     lib.ion_step_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                      _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp]
@@ -366,3 +369,22 @@ def stiff_cells(ws: torch.Tensor) -> int:
     """Cells of the last FP32 step that used `ws` with some W dt > 1,
     finished on the long path; synchronizes."""
     return int(ws[8:12].cpu().view(torch.int32)[0])
+
+
+def conservation(N: torch.Tensor, out: torch.Tensor, ncells: int | None = None,
+                 nplanes: int | None = None, target: float = 1.0) -> torch.Tensor:
+    """ion_conservation: writes max_c |sum_k N[k, c] - target| over the
+    first `ncells` cells of the (planes, ld) SoA N into the device scalar
+    `out` (float32)."""
+    if N.dtype not in (torch.float32, torch.float64):
+        raise ValueError("N must be float32 or float64")
+    _need(N, "N", N.dtype)
+    _need(out, "out", torch.float32, N.device)
+    if N.dim() != 2 or out.numel() < 1:
+        raise ValueError("N must be (planes, ld) and out non-empty")
+    n = N.shape[1] if ncells is None else int(ncells)
+    k = N.shape[0] if nplanes is None else int(nplanes)
+    dtype = ION_DTYPE_F32 if N.dtype == torch.float32 else ION_DTYPE_F64
+    _check(lib().ion_conservation(_ptr(N), N.shape[1], n, k, float(target), dtype, _ptr(out),
+                                  _stream(N)))
+    return out

@@ -1,0 +1,70 @@
+"""Multi-step runs of ion_step captured in one CUDA graph.
+
+A PIC code calls the ionization step once per time step with that step's
+field.  StepGraph records K such calls (and, optionally, the conservation
+diagnostic after each) into one CUDA graph, so that replaying K steps costs
+one graph launch instead of K times three kernel launches and their host
+argument checks.  Argument checking happens once, during capture; the graph
+then replays the same device pointers: the field tensors, populations,
+windows, dne and workspace must stay alive and in place.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import ionize
+
+
+def _prime(sp: ionize.Species, flags: int, device) -> None:
+    """One eager step on a few private cells, so that the library's one-time
+    per-kernel set-up (shared-memory limits, occupancy) is done before any
+    capture."""
+    n = 256
+    f64 = bool(flags & ionize.ION_F64_PLAIN)
+    dt = torch.float64 if f64 else torch.float32
+    E = torch.full((n,), 100.0, dtype=dt, device=device)
+    N = torch.zeros((sp.Z + 1, n), dtype=dt, device=device)
+    N[0] = 1.0
+    lo = torch.zeros(n, dtype=torch.uint8, device=device)
+    hi = torch.full((n,), min(sp.Z, 3), dtype=torch.uint8, device=device)
+    dne = torch.empty(n, dtype=dt, device=device)
+    ionize.step(sp, E, N, lo, hi, 0.05, dne, flags=flags)
+    torch.cuda.synchronize(device)
+
+
+class StepGraph:
+    """K = len(fields) steps: step s advances N, k_lo, k_hi by dt with the
+    field fields[s] and writes dne; with `conservation`, the largest
+    |sum_k N_k - 1| over the cells after step s lands in self.cons[s]."""
+
+    def __init__(self, sp: ionize.Species, fields, N: torch.Tensor, k_lo: torch.Tensor,
+                 k_hi: torch.Tensor, dne: torch.Tensor, dt: float,
+                 ws: torch.Tensor | None = None, flags: int = ionize.ION_F32,
+                 conservation: bool = True, eps_shift: float = 1e-6,
+                 degen_gap: float = 1e-3):
+        if not fields:
+            raise ValueError("at least one field")
+        dev = N.device
+        n = fields[0].numel()
+        if any(f.numel() != n for f in fields):
+            raise ValueError("every field must have the same number of cells")
+        self.steps = len(fields)
+        self.fields = list(fields)
+        self.ws = ws if ws is not None else ionize.workspace(n, flags, dev)
+        self.cons = torch.zeros(self.steps, dtype=torch.float32, device=dev)
+        _prime(sp, flags, dev)
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.graph(self.graph, stream=side):
+            for s, E in enumerate(self.fields):
+                ionize.step(sp, E, N, k_lo, k_hi, dt, dne, ws=self.ws, eps_shift=eps_shift,
+                            degen_gap=degen_gap, flags=flags)
+                if conservation:
+                    ionize.conservation(N, self.cons[s:s + 1], ncells=n)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        self.conservation = conservation
+
+    def replay(self) -> None:
+        """Enqueue the K steps on the current stream."""
+        self.graph.replay()

@@ -292,21 +292,56 @@ def mixed_batch(scale: float = 1.0, seed: int = 3, device="cpu"):
             for i, (sp, n) in enumerate(specs)]
 
 
-def krypton_beams(t: float, nz: int = 256, ny: int = 512, nx: int = 512,
-                  dx: float = 0.5, seed: int = 5, peak: float = 6000.0,
-                  lam: float = 0.8, device="cpu", scale=None) -> tuple:
-    """|E| of 16 seeded Gaussian beams at time t: each beam b has a unit
-    direction d_b, a centre, a waist w_b ~ U(4, 16) um and a phase phi_b;
-    E = S |sum_b exp(-rho_b^2/w_b^2) cos(k d_b.r - w t + phi_b)|, rho_b the
-    distance from the beam axis.  S scales the t = 0 maximum to `peak`
-    (pass the returned S back in for later times)."""
+def krypton_beam_terms(nz: int = 256, ny: int = 512, nx: int = 512, dx: float = 0.5,
+                       seed: int = 5, lam: float = 0.8, device="cpu",
+                       cells: torch.Tensor | None = None) -> tuple:
+    """The two standing patterns of 16 seeded Gaussian beams on an
+    nz x ny x nx grid (x fastest, cell centres at (i + 1/2) dx).  Beam b has
+    a unit direction d_b, a centre, a waist w_b ~ U(4, 16) um and a phase
+    phi_b; with g_b = exp(-rho_b^2/w_b^2) (rho_b the distance from the beam
+    axis) and theta_b = k d_b.r + phi_b, the field of the superposition is
+    sum_b g_b cos(theta_b - w t) = A cos(w t) + B sin(w t) with
+    A = sum_b g_b cos(theta_b), B = sum_b g_b sin(theta_b), since all beams
+    share lambda.  Returns (A, B) float64 for the cells `cells` (default:
+    the whole grid)."""
     dev = torch.device(device)
-    n = nz * ny * nx
-    c = torch.arange(n, device=dev, dtype=torch.int64)
-    ix, iy, iz = c % nx, (c // nx) % ny, c // (nx * ny)
-    r = torch.stack([(ix.to(torch.float64) + 0.5) * dx, (iy.to(torch.float64) + 0.5) * dx,
-                     (iz.to(torch.float64) + 0.5) * dx])
-    del ix, iy, iz, c
+    c = (torch.arange(nz * ny * nx, device=dev, dtype=torch.int64) if cells is None
+         else cells.to(dev, torch.int64))
+    x = ((c % nx).to(torch.float64) + 0.5) * dx
+    y = (((c // nx) % ny).to(torch.float64) + 0.5) * dx
+    z = ((c // (nx * ny)).to(torch.float64) + 0.5) * dx
+    del c
+    b = torch.arange(16, dtype=torch.int64)
+    d = torch.stack([normal(seed, 20 + k, b) for k in range(3)])
+    d = d / d.norm(dim=0, keepdim=True)
+    L = torch.tensor([nx * dx, ny * dx, nz * dx], dtype=torch.float64)
+    ctr = torch.stack([uniform(seed, 30 + k, b) for k in range(3)]) * L[:, None]
+    wb = 4.0 + 12.0 * uniform(seed, 40, b)
+    phi = 2 * math.pi * uniform(seed, 41, b)
+    kL = 2 * math.pi / lam
+    A = torch.zeros_like(x)
+    B = torch.zeros_like(x)
+    for j in range(16):
+        rx, ry, rz = x - float(ctr[0, j]), y - float(ctr[1, j]), z - float(ctr[2, j])
+        along = rx * float(d[0, j]) + ry * float(d[1, j]) + rz * float(d[2, j])
+        rho2 = rx * rx + ry * ry + rz * rz - along * along
+        del rx, ry, rz
+        g = torch.exp(-rho2 / float(wb[j]) ** 2)
+        theta = kL * along + float(phi[j])
+        A += g * torch.cos(theta)
+        B += g * torch.sin(theta)
+        del along, rho2, g, theta
+    return A, B
+
+
+def krypton_beams_direct(t: float, nz: int, ny: int, nx: int, dx: float = 0.5,
+                         seed: int = 5, lam: float = 0.8) -> torch.Tensor:
+    """The same superposition evaluated beam by beam at time t (float64,
+    unscaled, signed), for checking krypton_beam_terms on small grids."""
+    c = torch.arange(nz * ny * nx, dtype=torch.int64)
+    r = torch.stack([((c % nx).to(torch.float64) + 0.5) * dx,
+                     (((c // nx) % ny).to(torch.float64) + 0.5) * dx,
+                     ((c // (nx * ny)).to(torch.float64) + 0.5) * dx])
     b = torch.arange(16, dtype=torch.int64)
     d = torch.stack([normal(seed, 20 + k, b) for k in range(3)])
     d = d / d.norm(dim=0, keepdim=True)
@@ -316,18 +351,25 @@ def krypton_beams(t: float, nz: int = 256, ny: int = 512, nx: int = 512,
     phi = 2 * math.pi * uniform(seed, 41, b)
     kL = 2 * math.pi / lam
     omega = kL * C_UM_PER_FS
-    acc = torch.zeros(n, dtype=torch.float64, device=dev)
+    acc = torch.zeros(r.shape[1], dtype=torch.float64)
     for j in range(16):
-        dj = d[:, j].to(dev)
-        rel = r - ctr[:, j].to(dev)[:, None]
-        along = (rel * dj[:, None]).sum(0)
+        rel = r - ctr[:, j][:, None]
+        along = (rel * d[:, j][:, None]).sum(0)
         rho2 = (rel * rel).sum(0) - along * along
         acc += torch.exp(-rho2 / float(wb[j]) ** 2) * torch.cos(kL * along - omega * t + float(phi[j]))
-        del rel, along, rho2
-    acc = acc.abs()
-    if scale is None:
-        scale = peak / float(acc.max())
-    return (acc * scale).to(torch.float32), scale
+    return acc
+
+
+def krypton_scale(A: torch.Tensor, peak: float = 6000.0) -> float:
+    """S such that the t = 0 maximum of S |A| is `peak` GV/m."""
+    return peak / float(A.abs().max())
+
+
+def krypton_field(A: torch.Tensor, B: torch.Tensor, t: float, scale: float,
+                  lam: float = 0.8) -> torch.Tensor:
+    """|E| (GV/m, float32) = S |A cos(w t) + B sin(w t)| at time t (fs)."""
+    omega = 2 * math.pi / lam * C_UM_PER_FS
+    return (scale * (A * math.cos(omega * t) + B * math.sin(omega * t)).abs()).to(torch.float32)
 
 
 def krypton_initial(n: int, device="cpu") -> Workload:

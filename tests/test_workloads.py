@@ -65,3 +65,22 @@ def test_pulse_2d():
     w = 2 * math.pi * W.C_UM_PER_FS / 0.8
     peak = 2000 * abs(math.cos(w * 5.0))
     assert float(E.max()) <= peak + 1e-3
+
+
+def test_krypton_beam_terms_match_the_direct_sum():
+    """A cos(wt) + B sin(wt) equals the beam-by-beam superposition at any t."""
+    nz, ny, nx = 6, 10, 12
+    A, B = W.krypton_beam_terms(nz, ny, nx, dx=2.0)
+    omega = 2 * math.pi / 0.8 * W.C_UM_PER_FS
+    for t in (0.0, 0.37, 1.3, 2.45):
+        direct = W.krypton_beams_direct(t, nz, ny, nx, dx=2.0)
+        two = A * math.cos(omega * t) + B * math.sin(omega * t)
+        assert torch.allclose(two, direct, rtol=0, atol=1e-12 * 16)
+    # a subset of cells takes the grid's values there
+    cells = torch.tensor([0, 5, 77, nz * ny * nx - 1])
+    As, Bs = W.krypton_beam_terms(nz, ny, nx, dx=2.0, cells=cells)
+    assert torch.equal(As, A[cells]) and torch.equal(Bs, B[cells])
+    S = W.krypton_scale(A)
+    E0 = W.krypton_field(A, B, 0.0, S)
+    assert E0.dtype == torch.float32 and abs(float(E0.max()) - 6000.0) < 1e-3
+    assert float(E0.min()) >= 0.0
