@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-krypton", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -361,6 +362,84 @@ def main():
                    "max_abs_err_N_vs_oracle": bacc}
         del bjobs, bjobs_wl, pristine, bws
 
+    # -- surrogate form: Ar-like cells, rates from the tensor-core network ----
+    surrogate = None
+    if not args.no_surrogate:
+        from paper_2202_10647_gb300 import surrogate as S
+        sd4 = W.argon_like()
+        sp4 = ionize.Species(sd4.U, sd4.l, sd4.m)
+        t0 = time.time()
+        net4, tr4, bound4 = S.build(sp4)
+        torch.cuda.synchronize()
+        train_s = time.time() - t0
+        n4 = 33_554_432
+        wl4 = W.ladder_cells(sd4, n4, 4, device=dev)
+        N40, lo40, hi40 = wl4.N.clone(), wl4.lo.clone(), wl4.hi.clone()
+        dne4 = torch.empty(n4, device=dev)
+        ws4 = ionize.workspace(n4)
+
+        def r4():
+            wl4.N.copy_(N40)
+            wl4.lo.copy_(lo40)
+            wl4.hi.copy_(hi40)
+            flush.zero_()
+
+        def t4(fn, reps):
+            ts_ = []
+            for r_ in range(reps + 3):
+                r4()
+                a_ = torch.cuda.Event(enable_timing=True)
+                b_ = torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                fn()
+                b_.record(stream)
+                if r_ >= 3:
+                    ts_.append((a_, b_))
+            torch.cuda.synchronize()
+            return float(np.mean([a_.elapsed_time(b_) for a_, b_ in ts_]))
+
+        reps4 = max(5, min(30, args.steps // 10))
+        t_plain4 = t4(lambda: ionize.step(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4),
+                      reps4)
+        t_net4 = t4(lambda: net4.step(wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4), reps4)
+        n_net4, n_plain4, tmo4 = ionize.surrogate_counters(ws4)
+        acc4 = None
+        if rank == 0:
+            import oracle
+            ix4 = torch.tensor(sample_indices(n4, 4000, 6), device=dev)
+            r4()
+            Es4 = wl4.E[ix4].double().cpu().numpy()
+            Ns4 = wl4.N[:, ix4].double().cpu().numpy()
+            ls4, hs4 = wl4.lo[ix4].cpu().numpy(), wl4.hi[ix4].cpu().numpy()
+            net4.step(wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4)
+            Nnet = wl4.N[:, ix4].double().cpu().numpy()
+            r4()
+            ionize.step(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4)
+            Npl = wl4.N[:, ix4].double().cpu().numpy()
+            osp4 = oracle.Species(sd4.U, sd4.l, sd4.m)
+            No4, _, _, _ = oracle.step(osp4, Es4, Ns4, 0.05, ls4, hs4)
+            Wn4 = net4.rates(wl4.E[ix4].contiguous()).double().cpu().numpy()
+            Wo4 = oracle.rates(osp4, Es4, 0, sd4.Z)
+            big4 = Wo4 * 0.05 > 1e-12
+            rel4 = np.abs(Wn4[big4] / Wo4[big4] - 1.0)
+            acc4 = {"max_rel_rate_error": float(rel4.max()),
+                    "median_rel_rate_error": float(np.median(rel4)),
+                    "rate_error_over": "states with W dt > 1e-12 of 4000 sampled cells",
+                    "max_abs_err_N_vs_oracle_surrogate_form": float(np.abs(Nnet - No4).max()),
+                    "max_abs_err_N_vs_oracle_plain_fp32": float(np.abs(Npl - No4).max())}
+        surrogate = {"value": n4 / (t_net4 * 1e-3), "ms_per_step": t_net4,
+                     "plain_fp32": {"value": n4 / (t_plain4 * 1e-3), "ms_per_step": t_plain4},
+                     "gain_vs_plain": t_plain4 / t_net4,
+                     "cells": n4, "species": "Ar-like (Z=18)",
+                     "network": "1-64-64-18 GELU, bf16 weights, FP32 accumulation (tcgen05)",
+                     "train": {"seconds": train_s, "steps": tr4.steps, "pairs": 1 << 20,
+                               "final_loss": tr4.losses[-1][1]},
+                     "pop_tol": 1e-6,
+                     "cells_on_network_rates": n_net4 / n4,
+                     "cells_on_eq1_rates": n_plain4 / n4, "timeouts": tmo4,
+                     "accuracy": acc4}
+        del wl4, N40, lo40, hi40, dne4, ws4
+
     # -- Kr-like 512x512x256 cells, 50 steps captured in one CUDA graph -------
     krypton = None
     if not args.no_krypton:
@@ -378,6 +457,13 @@ def main():
         graphs = {name: multistep.StepGraph(ksp, kfields, kwl.N, kwl.lo, kwl.hi, kdne, 0.05,
                                             ws=kws, conservation=chk)
                   for name, chk in (("with_check", True), ("steps_only", False))}
+        knet = None
+        if not args.no_surrogate:
+            from paper_2202_10647_gb300 import surrogate as S
+            knet, _, _ = S.build(ksp)
+            graphs["surrogate_with_check"] = multistep.StepGraph(
+                ksp, kfields, kwl.N, kwl.lo, kwl.hi, kdne, 0.05, ws=kws, conservation=True,
+                surrogate=knet)
 
         def kreset():
             kwl.N.zero_()
@@ -400,6 +486,13 @@ def main():
                     ts_.append(a_.elapsed_time(b_))
             kres[name] = float(np.median(ts_))
         cons = graphs["with_check"].cons.cpu().numpy()
+        ksur = None
+        if "surrogate_with_check" in graphs:
+            kc = graphs["surrogate_with_check"].cons.cpu().numpy()
+            ksur = {"value": 50 * kn / (kres["surrogate_with_check"] * 1e-3),
+                    "ms_per_50_steps": kres["surrogate_with_check"],
+                    "max_abs_sum_N_minus_1": float(kc.max()),
+                    "network": "1-64-64-36 GELU, bf16 weights, FP32 accumulation (tcgen05)"}
         krypton = {"value": 50 * kn / (kres["with_check"] * 1e-3),
                    "ms_per_50_steps": kres["with_check"],
                    "value_steps_only": 50 * kn / (kres["steps_only"] * 1e-3),
@@ -410,8 +503,9 @@ def main():
                    "max_abs_sum_N_minus_1": {"after_step_1": float(cons[0]),
                                              "after_step_50": float(cons[-1]),
                                              "max": float(cons.max())},
-                   "windows_slid_fraction": float((kwl.lo > 0).double().mean())}
-        del graphs, kfields, kwl, kws, kdne
+                   "windows_slid_fraction": float((kwl.lo > 0).double().mean()),
+                   "surrogate_form": ksur}
+        del graphs, kfields, kwl, kws, kdne, knet
 
     # -- end to end through host buffers -------------------------------------
     e2e = None
@@ -505,6 +599,7 @@ def main():
                            "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9},
             "batched_mixed_species": batched,
             "krypton_beams_50_steps_graph": krypton,
+            "surrogate_argon": surrogate,
         },
         "accuracy": acc,
         "gpu_launches": 3 * args.steps,

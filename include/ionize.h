@@ -277,6 +277,127 @@ ION_API int ion_step_noalloc(const ion_species* sp, const void* E, void* N,
 ION_API int ion_conservation(const void* N, int64_t ld, int64_t ncells, int nplanes,
                              double target, int dtype, float* out_max, void* stream);
 
+/* ---- rate surrogate: network and training --------------------------------
+ * A small network maps the field magnitude to the logarithms of all Z rates
+ * of a species at once (the paper evaluates Eq. 1 directly; the surrogate is
+ * the learned alternative and is judged against it):
+ *   h1 = g(W1 x + b1), h2 = g(W2 h1 + b2), y = W3 h2 + b3,
+ * ION_MLP_HIDDEN = 64 hidden units, K <= ION_MAX_Z outputs, g the GELU in
+ * its tanh form g(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+ * Parameters are one device FP32 array in the order W1[64], b1[64],
+ * W2[64][64] (row o: weights into unit o), b2[64], W3[K][64], b3[K]
+ * (ion_mlp_nparams(K) values).  Samples are x[b] and targets t[b*K + k].
+ * The training calls below run on the GPU; all arrays are device arrays,
+ * 4-byte aligned; batches hold 1..2^24 samples. */
+#define ION_MLP_HIDDEN 64
+/* Forward pass in the inference arithmetic: W2, W3, h1 and h2 rounded to
+ * bf16 and the SFU tanh, as in the tensor-core kernels; the backward pass
+ * treats the rounding as the identity (straight-through).  Without it the
+ * forward pass is plain FP32 with tanhf. */
+#define ION_MLP_BF16 0x1
+
+/* Parameter count for K outputs (ION_EINVAL if K is outside 1..ION_MAX_Z). */
+ION_API int64_t ion_mlp_nparams(int K);
+
+/* Workspace bytes of ion_mlp_loss_grad (0 for arguments out of range). */
+ION_API size_t ion_mlp_workspace_bytes(int K, int64_t B);
+
+/* ion_mlp_loss_grad -- L = (1/(B K)) sum_b sum_k (y_bk - t_bk)^2 and dL/dP.
+ *   P     device [ion_mlp_nparams(K)] parameters (read).
+ *   x, t  device [B] inputs and [B*K] targets.
+ *   flags 0 or ION_MLP_BF16.
+ *   grad  device [ion_mlp_nparams(K)], overwritten with dL/dP.
+ *   loss  device float or NULL: L.
+ *   workspace  device, 256-byte aligned, >= ion_mlp_workspace_bytes(K, B).
+ * The batch sums are taken in a fixed order: equal inputs give equal bits.
+ * Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_mlp_loss_grad(const float* P, int K, const float* x, const float* t,
+                              int64_t B, int flags, float* grad, float* loss,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* ion_mlp_adam -- one Adam step (t >= 1) on n parameters in place:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * P -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps).  m and v start at zero.
+ * Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_mlp_adam(float* P, const float* grad, float* m, float* v, int64_t n,
+                         float lr, float beta1, float beta2, float eps, int t,
+                         void* stream);
+
+/* ion_mlp_forward -- y[b*K + k] for B inputs on CUDA cores (FP32, or with
+ * ION_MLP_BF16 the inference arithmetic); the reference the tensor-core
+ * surrogate kernels are checked against.  Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_mlp_forward(const float* P, int K, const float* x, int64_t B, int flags,
+                            float* y, void* stream);
+
+/* ---- rate surrogate: inference -------------------------------------------
+ * A trained network (parameters as above, K = Z outputs) becomes an
+ * ion_surrogate: W2 and W3 in bf16 laid out for the tensor cores, the other
+ * parameters in FP32.  Its kernels evaluate the network for 128 cells at a
+ * time: layer 1 (one input) and the GELUs on the CUDA cores, layers 2 and 3
+ * as 128 x 64 x 64 and 128 x N x 64 bf16 products with FP32 accumulation on
+ * the tensor cores (tcgen05, accumulators in tensor memory).
+ *
+ * Input and output scaling (ion_surrogate_norm):
+ *   x = 2 (log2|E| - log2E_min) / (log2E_max - log2E_min) - 1,
+ *   log2 W_k [1/fs] = y_mean[k] + y_scale[k] * y_k,  W_k = 0 where that is
+ *   below y_floor.
+ * The network is trusted only for log2E_min <= log2|E| <= log2E_max, and
+ * only where its validation error bound allows (ion_step_surrogate). */
+typedef struct ion_surrogate ion_surrogate; /* opaque, owned by the library */
+
+typedef struct {
+  double log2E_min, log2E_max; /* trained range of log2(|E| / (GV/m)) */
+  double y_floor;              /* log2 W below this is W = 0 */
+  double y_mean[ION_MAX_Z];
+  double y_scale[ION_MAX_Z];
+} ion_surrogate_norm;
+
+/* ion_surrogate_create -- a surrogate of species `sp` (K = Z outputs).
+ *   P      device FP32 [ion_mlp_nparams(Z)] trained parameters (read during
+ *          the call; synchronous copy).
+ *   norm   host, the scaling above; log2E_min < log2E_max.
+ *   bound  host [nbins * Z] or NULL: bound[b*Z + k] >= max |log2 W_k(net) -
+ *          log2 W_k(Eq. 1)| over the inputs of bin b, the bins splitting
+ *          [log2E_min, log2E_max] into nbins equal parts (1 <= nbins <=
+ *          65536), values clamped below at y_floor on both sides.  NULL
+ *          trusts the network everywhere in range (bound 0).
+ * The surrogate keeps its own copy of the species table.  Allocates device
+ * memory.  Errors: ION_EINVAL, ION_ENOMEM, ION_ECUDA. */
+ION_API int ion_surrogate_create(const ion_species* sp, const float* P,
+                                 const ion_surrogate_norm* norm, const float* bound,
+                                 int nbins, ion_surrogate** out);
+ION_API int ion_surrogate_destroy(ion_surrogate* s);
+
+/* ion_surrogate_rates -- the network's W_k(|E_c|) in 1/fs for every state
+ * k < Z of every cell: W_out[k*ldw + c] (device, float, ldw >= ncells).
+ * No range check: cells outside the trained range get the network's
+ * extrapolation.  Errors: ION_EINVAL, ION_ECUDA.  (A bounded wait for the
+ * tensor cores that gives up leaves NaN in the rates of its cells.) */
+ION_API int ion_surrogate_rates(const ion_surrogate* s, const float* E, int64_t ncells,
+                                float* W_out, int64_t ldw, void* stream);
+
+/* ion_step_surrogate -- ion_step (ION_F32) with the window's rates taken
+ * from the network where it can be trusted: for a cell with |E| in the
+ * trained range, the network's rates W_r of the window's w-1 transitions
+ * give a bound on the population error of the step,
+ *   2 dt sum_r (max(W_r, 2^y_floor) (2^bound - 1) + 2^y_floor)
+ * (a perturbation of the rate matrix by dA moves the solution of Eq. 3 by
+ * at most |dA| in the 1-norm); if it is at most pop_tol the network's rates
+ * are used, otherwise (and outside the range) the rates of Eq. 1.  The
+ * update itself is ion_step's (Taylor or Bateman form, FP64 coefficients for
+ * nearly degenerate rate pairs, window slide).  Arguments as ion_step with
+ * FP32 arrays; pop_tol >= 0.  Workspace: ion_step_workspace_bytes(ncells,
+ * ION_F32); after the call its header holds, besides the words described
+ * for ion_step, word 3: cells that took the network's rates, word 4: cells
+ * that took the rates of Eq. 1, word 5: non-zero if a bounded wait for the
+ * tensor cores gave up (the results of the call are then invalid).
+ * Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N, int64_t ld,
+                               int64_t ncells, double dt_fs, uint8_t* k_lo, uint8_t* k_hi,
+                               float* dne, const float* n_gas, const ion_step_opts* opts,
+                               double pop_tol, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 ION_API const char* ion_last_error(void);
 

@@ -296,6 +296,35 @@ int check_workspace(void* workspace, size_t have, size_t need) {
   return ION_OK;
 }
 
+}  // namespace
+
+int ion::species_info(const ion_species* sp, SpeciesInfo* out) {
+  const int rc = check_species(sp);
+  if (rc) return rc;
+  out->device = sp->device;
+  out->num_sms = sp->num_sms;
+  out->Z = sp->Z;
+  out->host = &sp->host;
+  out->dev = sp->dev;
+  return ION_OK;
+}
+
+int ion::policy_from_args(double dt_fs, const ion_step_opts* opts, int flags, Policy* pol) {
+  return make_policy(dt_fs, opts, flags, pol);
+}
+
+int ion::job_from_args(const ion_species* sp, const void* E, void* N, int64_t ld,
+                       int64_t ncells, uint8_t* k_lo, uint8_t* k_hi, void* dne,
+                       const void* n_gas, bool f64, int Q, const char* who, JobIO* J) {
+  return make_job(sp, E, N, ld, ncells, k_lo, k_hi, dne, n_gas, f64, Q, who, J);
+}
+
+int ion::workspace_ok(void* workspace, size_t have, size_t need) {
+  return check_workspace(workspace, have, need);
+}
+
+namespace {
+
 int run_batch(const ion_batch_job* jobs, int njobs, double dt_fs, const ion_step_opts* opts,
               int flags, const ion_launch_shape* shape, void* workspace, size_t ws_bytes,
               void* stream) {

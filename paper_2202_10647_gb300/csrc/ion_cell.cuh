@@ -81,30 +81,24 @@ __device__ __forceinline__ void warp_append(uint32_t* counter, uint32_t* queue,
 }
 
 // ---------------------------------------------------------------------------
-// Full update of one cell whose window populations v[0..w-1] are loaded
-// (w <= WM): rates, Taylor or Bateman form, window slide, stores.  Returns
-// true (and stores nothing) if the cell goes to the FP64 queue.
+// Update of one cell whose window populations v[0..w-1] and rates
+// lam[r] = W_{lo+r} dt (r < w-1; 0 beyond) are known (2 <= w <= WM): Taylor
+// or Bateman form, window slide, stores.  Returns true (and stores nothing)
+// if the cell goes to the FP64 queue.
 // ---------------------------------------------------------------------------
-template <class F, int WM>
-__device__ __forceinline__ bool finish_cell(const JobIO& J, const Policy& pol,
-                                            const typename F::Staged& tab, int c,
-                                            typename F::T Ec, int lo, int hi,
-                                            typename F::T (&v)[WM], bool allow_fb) {
-  using T = typename F::T;
+template <typename T, int WM>
+__device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, int c, int lo,
+                                            int hi, T (&v)[WM], const T (&lam)[WM],
+                                            bool allow_fb) {
   T* __restrict__ N = static_cast<T*>(J.N);
   const int w = hi - lo + 1;
   T dne = T(0);
   int nlo = lo, nhi = hi;
   if constexpr (WM >= 2) {
     if (w >= 2) {
-      const typename F::Field f = F::field(Ec);
-      T lam[WM];
       T lmax = T(0);
 #pragma unroll
-      for (int r = 0; r < WM; ++r) {
-        lam[r] = (r < w - 1 && !pol.zero_dt) ? F::rate(tab, lo + r, f) : T(0);
-        lmax = fmax(lmax, lam[r]);
-      }
+      for (int r = 0; r < WM; ++r) lmax = fmax(lmax, lam[r]);
       if (lmax <= DDParams<T>::prop_max) {
         dne = taylor_propagate<T, WM>(v, lam, w, lmax);
       } else {
@@ -131,6 +125,27 @@ __device__ __forceinline__ bool finish_cell(const JobIO& J, const Policy& pol,
     J.hi[c] = (uint8_t)nhi;
   }
   return false;
+}
+
+// Full update of one cell whose window populations are loaded: the rates of
+// Eq. 1, then update_cell.
+template <class F, int WM>
+__device__ __forceinline__ bool finish_cell(const JobIO& J, const Policy& pol,
+                                            const typename F::Staged& tab, int c,
+                                            typename F::T Ec, int lo, int hi,
+                                            typename F::T (&v)[WM], bool allow_fb) {
+  using T = typename F::T;
+  const int w = hi - lo + 1;
+  T lam[WM];
+#pragma unroll
+  for (int r = 0; r < WM; ++r) lam[r] = T(0);
+  if (w >= 2 && !pol.zero_dt) {
+    const typename F::Field f = F::field(Ec);
+#pragma unroll
+    for (int r = 0; r < WM; ++r)
+      if (r < w - 1) lam[r] = F::rate(tab, lo + r, f);
+  }
+  return update_cell<T, WM>(J, pol, c, lo, hi, v, lam, allow_fb);
 }
 
 // The same, loading the window from global memory; W bounds the width.

@@ -13,7 +13,10 @@ namespace ion {
 constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
 constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
 constexpr int kHdrStiff = 2;     // stiff-cell records written by the streaming kernel
-constexpr int kHdrWords = 3;
+constexpr int kHdrSurrogate = 3; // surrogate step: cells whose rates came from the network
+constexpr int kHdrPlain = 4;     // surrogate step: cells that took the rates of Eq. 1
+constexpr int kHdrTimeout = 5;   // surrogate step: non-zero if a bounded wait gave up
+constexpr int kHdrWords = 6;
 constexpr size_t kHdrBytes = 256;
 
 // Largest number of species one batched launch advances.
@@ -83,10 +86,27 @@ void bind_workspace(Scratch& s, void* ws, int64_t ncells);
 // (api.cu).
 int set_error(int code, const char* fmt, ...);
 
+// Argument checking shared by the entry points (api.cu); each returns ION_OK
+// or sets the thread's error message and returns the ION_E* code.
+struct SpeciesInfo {
+  int device, num_sms, Z;
+  const SpeciesTable* host;  // host copy
+  const SpeciesTable* dev;   // device copy
+};
+int species_info(const ion_species* sp, SpeciesInfo* out);
+int policy_from_args(double dt_fs, const ion_step_opts* opts, int flags, Policy* pol);
+int job_from_args(const ion_species* sp, const void* E, void* N, int64_t ld, int64_t ncells,
+                  uint8_t* k_lo, uint8_t* k_hi, void* dne, const void* n_gas, bool f64, int Q,
+                  const char* who, JobIO* J);
+int workspace_ok(void* workspace, size_t have, size_t need);
+
 // Launchers.  They only enqueue; the caller has validated.  `a.job[j].chunk0`
 // and `a.nchunks` are filled in by launch_batch_f32.
 cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms,
                              cudaStream_t s);
+// The FP64-coefficient pass over the cells queued by a previous kernel of the
+// same call (step_f32.cu).
+cudaError_t launch_fb_f32(const BatchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_step_f64(const JobIO& job, const Policy& pol, uint32_t* hdr,
                             cudaStream_t s);
 LaunchShape default_shape();

@@ -753,13 +753,15 @@ cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms
   if ((e = cudaLaunchKernel(v->fn, blocks, v->W * 32, args, smem, s)) != cudaSuccess) return e;
   ion_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_fb_f32(a, num_sms, s);
+}
+
+cudaError_t launch_fb_f32(const BatchArgs& a, int num_sms, cudaStream_t s) {
   const bool need_fb = (a.pol.flags & ION_NO_FP64_FALLBACK) == 0 &&
                        ((a.pol.flags & ION_FORCE_FP64_COEF) != 0 || a.pol.gap > 0.0);
-  if (need_fb) {
-    ion_fb_kernel<<<2 * num_sms, 128, 0, s>>>(a);
-    e = cudaGetLastError();
-  }
-  return e;
+  if (!need_fb) return cudaSuccess;
+  ion_fb_kernel<<<2 * num_sms, 128, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace ion

@@ -1,0 +1,722 @@
+// surrogate.cu -- the rate surrogate at inference on the tensor cores.
+//
+// One CTA of 128 threads owns a tile of 128 cells at a time (thread t <->
+// cell t of the tile <-> row t of the MMAs <-> lane t of tensor memory):
+//   1. each thread evaluates layer 1 of its cell (one input, 64 GELUs) and
+//      writes h1 as bf16 into shared memory in the 128-byte-swizzled K-major
+//      layout the tensor cores read;
+//   2. one thread issues layer 2 as four 128x64x16 tcgen05.mma (bf16 in, FP32
+//      accumulators in tensor memory) and commits them to an mbarrier;
+//   3. every thread reads its row of the accumulators (tcgen05.ld), adds b2,
+//      applies the GELU and writes h2 over h1;
+//   4. layer 3 likewise (N = the output count padded to 16, 32, 48 or 64),
+//      reusing the same accumulator columns;
+//   5. the outputs, scaled to log2 W, are staged column-major in shared
+//      memory (conflict-free for any window position), and each thread
+//      finishes its cell: ion_surrogate_rates writes all Z rates,
+//      ion_step_surrogate picks the window's rates (network or Eq. 1, by the
+//      validation bound) and runs the update of ion_step.
+// Waits on the mbarrier are bounded; a wait that gives up marks the call as
+// failed (header word / NaN rates), frees the tensor memory and returns.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ion_cell.cuh"
+#include "ion_step.cuh"
+#include "ionize.h"
+#include "mlp_device.cuh"
+
+namespace ion {
+namespace sg {
+
+using mlp::H;
+
+constexpr int kM = 128;            // cells per tile = MMA M = threads per CTA
+constexpr uint32_t kTmemCols = 64; // accumulator columns (layer 3 reuses them)
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Scalars and short vectors of the network and its scaling.
+struct Consts {
+  float W1[H], b1[H], b2[H], b3[64];
+  float ymean[64], yscale[64];
+  float xa, xb;        // x = xa log2|E| + xb
+  float l2lo, l2hi;    // trusted log2|E| range
+  float yfloor;        // log2 W below this: W = 0
+  float bin_a, bin_b;  // bin = floor(bin_a log2|E| + bin_b)
+  int nbins;
+  int Z, KP;
+};
+
+// Device image of a surrogate (one allocation).
+struct Dev {
+  uint8_t W2img[64 * 128];  // layer-2 B operand: 64 rows (units) x 64 bf16 (K)
+  uint8_t W3img[64 * 128];  // layer-3 B operand: KP rows, zero-padded
+  Consts k;
+  SpeciesTable tab;
+};
+
+// Byte offset of element (row r, k) of a K-major bf16 tile with 64 elements
+// (128 bytes) per row in the 128-byte swizzle: 8-row groups of 1024 bytes,
+// the 16-byte chunk index XORed with the row within the group.
+__host__ __device__ constexpr uint32_t sw128_offset(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) +
+                    ((k & 7) << 1));
+}
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset 16
+// (unused by the swizzled K-major layout), stride byte offset 1024 (one
+// 8-row group), descriptor version 1 (bit 46), 128-byte swizzle (2 << 61).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulators (bit 4), bf16 A
+// (bit 7) and B (bit 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// Bounded wait for the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 16 accumulator columns of this thread's lane.  The wait takes the
+// registers as operands so that no use is scheduled before it.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// ---- shared-memory plan ---------------------------------------------------
+struct Plan {
+  uint32_t y_bytes;  // A tile (16 KB) / output staging (KP x 128 floats)
+  uint32_t w2, w3, consts, tab, bar, slot, total;
+};
+
+__host__ __device__ constexpr Plan plan_of(int KP) {
+  Plan p{};
+  p.y_bytes = (uint32_t)(KP * 512 > 16384 ? KP * 512 : 16384);
+  p.w2 = p.y_bytes;
+  p.w3 = p.w2 + 8192;
+  p.consts = p.w3 + (uint32_t)KP * 128;
+  p.tab = p.consts + (uint32_t)((sizeof(Consts) + 15) / 16 * 16);
+  p.bar = p.tab + (uint32_t)((sizeof(StagedF32) + 15) / 16 * 16);
+  p.slot = p.bar + 8;
+  p.total = p.slot + 8 + 1024;  // + slack for aligning the base to 1024
+  return p;
+}
+
+struct StepArgs {
+  JobIO J;
+  Policy pol;
+  Scratch ws;
+  float pop_tol;
+  const float* bound;  // [nbins][Z] of 2^bound - 1, or nullptr
+  float* W_out;        // rates mode
+  int64_t ldw;
+  int64_t ncells;
+  const float* E;
+};
+
+template <int W>
+__device__ __forceinline__ bool step_cell(const StepArgs& a, int c, int lo, int hi,
+                                          const float (&lam6)[ION_MAX_WINDOW]) {
+  const float* __restrict__ N = static_cast<const float*>(a.J.N);
+  float v[W], lam[W];
+  const float* p = N + (int64_t)lo * a.J.ld + c;
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    v[r] = __ldcs(p);
+    p += a.J.ld;
+    lam[r] = lam6[r];
+  }
+  return update_cell<float, W>(a.J, a.pol, c, lo, hi, v, lam, true);
+}
+
+// Counts the lanes with `take` set into *counter (one atomic per warp).
+__device__ __forceinline__ void warp_count(uint32_t* counter, bool take) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(counter, (unsigned)__popc(m));
+}
+
+template <bool Step, int KP>
+__global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ dev,
+                                                       const __grid_constant__ StepArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr Plan P = plan_of(KP);
+  // align the base to 1024 bytes (the swizzle atoms)
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  unsigned char* A = base;  // A tile, then the output staging Y[k][128]
+  float* Y = reinterpret_cast<float*>(base);
+  Consts& K = *reinterpret_cast<Consts*>(base + P.consts);
+  StagedF32& tab = *reinterpret_cast<StagedF32*>(base + P.tab);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + P.bar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(base + P.slot);
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+
+  // stage the operands and constants
+  {
+    const uint4* s2 = reinterpret_cast<const uint4*>(dev->W2img);
+    uint4* d2 = reinterpret_cast<uint4*>(base + P.w2);
+    for (int i = t; i < 8192 / 16; i += kM) d2[i] = s2[i];
+    const uint4* s3 = reinterpret_cast<const uint4*>(dev->W3img);
+    uint4* d3 = reinterpret_cast<uint4*>(base + P.w3);
+    for (int i = t; i < KP * 128 / 16; i += kM) d3[i] = s3[i];
+    const uint32_t* sc = reinterpret_cast<const uint32_t*>(&dev->k);
+    uint32_t* dc = reinterpret_cast<uint32_t*>(&K);
+    for (int i = t; i < (int)(sizeof(Consts) / 4); i += kM) dc[i] = sc[i];
+    stage_f32(&dev->tab, a.pol.log2dt, &tab);
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t sA = smem_u32(A), sW2 = smem_u32(base + P.w2), sW3 = smem_u32(base + P.w3);
+  const uint32_t sbar = smem_u32(bar);
+  const int Z = K.Z;
+  const float log2dt = (float)a.pol.log2dt;
+  unsigned char* row = A + (t >> 3) * 1024 + (t & 7) * 128;
+
+  uint32_t phase = 0;
+  bool failed = false;
+  const int64_t ntiles = (a.ncells + kM - 1) / kM;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c = tile * kM + t;
+    const bool on = c < a.ncells;
+    if (failed) {  // after a timeout: no tensor-core work, mark the outputs
+      if (!Step && on)
+        for (int k = 0; k < Z; ++k) a.W_out[(int64_t)k * a.ldw + c] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    __syncthreads();  // every thread is done with the previous tile's Y
+    const float Eabs = on ? fabsf(a.E[c]) : 1.0f;
+    const bool pos = Eabs > (float)kEmin && Eabs < INFINITY;
+    const float l2 = log2f(pos ? Eabs : 1.0f);
+    const float x = fminf(fmaxf(fmaf(K.xa, l2, K.xb), -1.0f), 1.0f);
+    // layer 1 -> A row t
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = mlp::gelu<true>(fmaf(K.W1[8 * q + j], x, K.b1[8 * q + j]));
+      const uint4 pk = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
+                                  pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+      *reinterpret_cast<uint4*>(row + (((q ^ (t & 7)) & 7) << 4)) = pk;
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_bf16(tmem, sw128_desc(sA + kk * 32), sw128_desc(sW2 + kk * 32), idesc_bf16(kM, H),
+                 kk > 0 ? 1u : 0u);
+      mma_commit(sbar);
+    }
+    bool ok = mbar_wait(sbar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      if (!Step && on)
+        for (int k = 0; k < Z; ++k) a.W_out[(int64_t)k * a.ldw + c] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    tc_fence_after();
+    // layer 2 epilogue: h2 = g(acc + b2) -> A row t (layer 2 has read A)
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      float v[16];
+      tmem_ld16(tlane + ch * 16, v);
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int u = ch * 16 + half * 8 + j;
+          h[j] = mlp::gelu<true>(v[half * 8 + j] + K.b2[u]);
+        }
+        const int q = ch * 2 + half;
+        const uint4 pk = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
+                                    pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+        *reinterpret_cast<uint4*>(row + (((q ^ (t & 7)) & 7) << 4)) = pk;
+      }
+    }
+    tc_fence_before();
+    fence_proxy_async();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_bf16(tmem, sw128_desc(sA + kk * 32), sw128_desc(sW3 + kk * 32), idesc_bf16(kM, KP),
+                 kk > 0 ? 1u : 0u);
+      mma_commit(sbar);
+    }
+    ok = mbar_wait(sbar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      if (!Step && on)
+        for (int k = 0; k < Z; ++k) a.W_out[(int64_t)k * a.ldw + c] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    tc_fence_after();
+    // layer 3 epilogue: log2 W_k = ymean + yscale (acc + b3) -> Y[k][t]
+    // (layer 3 has read A, so Y may overwrite it)
+#pragma unroll
+    for (int ch = 0; ch < KP / 16; ++ch) {
+      float v[16];
+      tmem_ld16(tlane + ch * 16, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int k = ch * 16 + j;
+        Y[k * kM + t] = fmaf(K.yscale[k], v[j] + K.b3[k], K.ymean[k]);
+      }
+    }
+    tc_fence_before();
+    if constexpr (!Step) {
+      if (on)
+        for (int k = 0; k < Z; ++k) {
+          const float s = Y[k * kM + t];
+          a.W_out[(int64_t)k * a.ldw + c] = s < K.yfloor ? 0.0f : exp2f(s);
+        }
+    } else {
+      const JobIO& J = a.J;
+      int lo = 0, hi = 0;
+      bool valid = false;
+      if (on) {
+        lo = J.lo[c];
+        hi = J.hi[c];
+        valid = window_ok(lo, hi, J.Z);
+        if (!valid) atomicAdd(&a.ws.hdr[kHdrInvalid], 1u);
+      }
+      const int w = hi - lo + 1;
+      float lam[ION_MAX_WINDOW];
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r) lam[r] = 0.0f;
+      bool net = false, plain = false;
+      if (valid && w >= 2 && !a.pol.zero_dt) {
+        const bool in_range = pos && l2 >= K.l2lo && l2 <= K.l2hi;
+        int bin = (int)floorf(fmaf(K.bin_a, l2, K.bin_b));
+        bin = min(max(bin, 0), K.nbins - 1);
+        const float wfloor = exp2f(K.yfloor + log2dt);
+        float err = 0.0f;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW - 1; ++r) {
+          if (r < w - 1) {
+            const int k = lo + r;
+            const float s = Y[k * kM + t];
+            lam[r] = s < K.yfloor ? 0.0f : ex2_approx(s + log2dt);
+            const float beta = a.bound ? a.bound[bin * Z + k] : 0.0f;
+            err += 2.0f * fmaf(fmaxf(lam[r], wfloor), beta, wfloor);
+          }
+        }
+        net = in_range && err <= a.pop_tol;
+        if (!net) {
+          plain = true;
+          const FieldF32 f = field_f32(a.E[c]);
+#pragma unroll
+          for (int r = 0; r < ION_MAX_WINDOW - 1; ++r)
+            if (r < w - 1) lam[r] = rate_dt_f32(tab, lo + r, f);
+        }
+      }
+      warp_count(&a.ws.hdr[kHdrSurrogate], net);
+      warp_count(&a.ws.hdr[kHdrPlain], plain);
+      bool fb = false;
+      if (valid) {
+        switch (w) {
+          case 1:
+            fb = step_cell<1>(a, (int)c, lo, hi, lam);
+            break;
+          case 2:
+            fb = step_cell<2>(a, (int)c, lo, hi, lam);
+            break;
+          case 3:
+            fb = step_cell<3>(a, (int)c, lo, hi, lam);
+            break;
+          case 4:
+            fb = step_cell<4>(a, (int)c, lo, hi, lam);
+            break;
+          case 5:
+            fb = step_cell<5>(a, (int)c, lo, hi, lam);
+            break;
+          default:
+            fb = step_cell<6>(a, (int)c, lo, hi, lam);
+            break;
+        }
+      }
+      warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb, (uint32_t)c, 0);
+    }
+  }
+  // leave: tensor memory is freed by the warp that allocated it once every
+  // read of it (and, after a timeout, the pending MMAs) are done
+  tc_fence_before();
+  __syncthreads();
+  if (failed && t == 0) {
+    if (a.ws.hdr) atomicAdd(&a.ws.hdr[kHdrTimeout], 1u);
+    mbar_wait(sbar, phase ^ 1u);  // the commit still pending, if it ever lands
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+}  // namespace sg
+}  // namespace ion
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct ion_surrogate {
+  int device, num_sms, Z, KP, nbins;
+  int fit_rates, fit_step;  // resident CTAs per SM of the two kernels
+  ion::sg::Dev* dev;
+  float* bound;  // device [nbins][Z] of 2^bound - 1, or nullptr
+};
+
+namespace {
+
+using ion::sg::Dev;
+using ion::sg::StepArgs;
+
+// Round to nearest even, as __float2bfloat16_rn does.
+uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+template <bool Step>
+const void* kernel_of(int KP) {
+  switch (KP) {
+    case 16:
+      return reinterpret_cast<const void*>(&ion::sg::surrogate_kernel<Step, 16>);
+    case 32:
+      return reinterpret_cast<const void*>(&ion::sg::surrogate_kernel<Step, 32>);
+    case 48:
+      return reinterpret_cast<const void*>(&ion::sg::surrogate_kernel<Step, 48>);
+    default:
+      return reinterpret_cast<const void*>(&ion::sg::surrogate_kernel<Step, 64>);
+  }
+}
+
+// Sets the shared-memory limit and measures residency; refuses shapes whose
+// resident CTAs could ask for more tensor memory than an SM has (512
+// columns), so no allocation ever has to wait.
+cudaError_t prepare(const void* fn, int KP, int* fit) {
+  const size_t smem = ion::sg::plan_of(KP).total;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, fn, ion::sg::kM, smem);
+  if (e != cudaSuccess) return e;
+  if (*fit < 1 || *fit * (int)ion::sg::kTmemCols > 512) return cudaErrorInvalidConfiguration;
+  return cudaSuccess;
+}
+
+cudaError_t launch(const ion_surrogate* s, bool step, const StepArgs& a, cudaStream_t st) {
+  const int64_t ntiles = (a.ncells + ion::sg::kM - 1) / ion::sg::kM;
+  if (ntiles == 0) return cudaSuccess;
+  const int fit = step ? s->fit_step : s->fit_rates;
+  const int64_t cap = (int64_t)fit * s->num_sms;
+  const int blocks = (int)(ntiles < cap ? ntiles : cap);
+  const void* fn = step ? kernel_of<true>(s->KP) : kernel_of<false>(s->KP);
+  const Dev* dev = s->dev;
+  void* args[] = {(void*)&dev, (void*)&a};
+  return cudaLaunchKernel(fn, blocks, ion::sg::kM, args, ion::sg::plan_of(s->KP).total, st);
+}
+
+int check_surrogate(const ion_surrogate* s) {
+  if (!s || !s->dev) return ion::set_error(ION_EINVAL, "surrogate is NULL or destroyed");
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess || d != s->device)
+    return ion::set_error(ION_EINVAL, "the surrogate lives on device %d; make it current",
+                          s->device);
+  return ION_OK;
+}
+
+bool al4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int ion_surrogate_create(const ion_species* sp, const float* P, const ion_surrogate_norm* norm,
+                         const float* bound, int nbins, ion_surrogate** out) {
+  using namespace ion;
+  if (!out) return set_error(ION_EINVAL, "out is NULL");
+  *out = nullptr;
+  SpeciesInfo si;
+  int rc = species_info(sp, &si);
+  if (rc) return rc;
+  if (!P || !norm) return set_error(ION_EINVAL, "P and norm must be non-NULL");
+  if (!(norm->log2E_min < norm->log2E_max) || !std::isfinite(norm->log2E_min) ||
+      !std::isfinite(norm->log2E_max) || !std::isfinite(norm->y_floor))
+    return set_error(ION_EINVAL, "norm: need finite log2E_min < log2E_max and y_floor");
+  if (bound && (nbins < 1 || nbins > 65536))
+    return set_error(ION_EINVAL, "nbins=%d outside [1, 65536]", nbins);
+  if (!bound) nbins = 1;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != si.device)
+    return set_error(ION_EINVAL, "the species lives on device %d; make it current", si.device);
+  const int Z = si.Z, KP = mlp::padded_out(Z), np = mlp::nparams(Z);
+  for (int k = 0; k < Z; ++k)
+    if (!std::isfinite(norm->y_mean[k]) || !(norm->y_scale[k] > 0.0) ||
+        !std::isfinite(norm->y_scale[k]))
+      return set_error(ION_EINVAL, "norm: y_mean[%d] must be finite, y_scale[%d] > 0", k, k);
+  std::vector<float> h((size_t)np);
+  cudaError_t e = cudaMemcpy(h.data(), P, sizeof(float) * np, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess)
+    return set_error(ION_ECUDA, "reading the parameters: %s", cudaGetErrorString(e));
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(h[i])) return set_error(ION_EINVAL, "parameter %d is not finite", i);
+  std::vector<float> beta((size_t)nbins * Z, 0.0f);
+  if (bound)
+    for (size_t i = 0; i < beta.size(); ++i) {
+      if (!(bound[i] >= 0.0f) || !std::isfinite(bound[i]))
+        return set_error(ION_EINVAL, "bound[%zu] must be finite and >= 0", i);
+      beta[i] = (float)(std::exp2((double)bound[i]) - 1.0);
+    }
+  Dev* img = new (std::nothrow) Dev();
+  if (!img) return set_error(ION_ENOMEM, "host allocation failed");
+  std::memset(img, 0, sizeof(Dev));
+  auto put = [](uint8_t* dst, int r, int k, float v) {
+    const uint16_t b = to_bf16(v);
+    std::memcpy(dst + sg::sw128_offset(r, k), &b, 2);
+  };
+  for (int o = 0; o < mlp::H; ++o)
+    for (int k = 0; k < mlp::H; ++k) put(img->W2img, o, k, h[mlp::off_W2() + o * mlp::H + k]);
+  for (int r = 0; r < KP; ++r)
+    for (int k = 0; k < mlp::H; ++k)
+      put(img->W3img, r, k, r < Z ? h[mlp::off_W3() + r * mlp::H + k] : 0.0f);
+  sg::Consts& c = img->k;
+  for (int i = 0; i < mlp::H; ++i) {
+    c.W1[i] = h[mlp::off_W1() + i];
+    c.b1[i] = h[mlp::off_b1() + i];
+    c.b2[i] = h[mlp::off_b2() + i];
+  }
+  for (int k = 0; k < Z; ++k) {
+    c.b3[k] = h[mlp::off_b3(Z) + k];
+    c.ymean[k] = (float)norm->y_mean[k];
+    c.yscale[k] = (float)norm->y_scale[k];
+  }
+  const double span = norm->log2E_max - norm->log2E_min;
+  c.xa = (float)(2.0 / span);
+  c.xb = (float)(-1.0 - norm->log2E_min * 2.0 / span);
+  c.l2lo = (float)norm->log2E_min;
+  c.l2hi = (float)norm->log2E_max;
+  c.yfloor = (float)norm->y_floor;
+  c.bin_a = (float)(nbins / span);
+  c.bin_b = (float)(-norm->log2E_min * nbins / span);
+  c.nbins = nbins;
+  c.Z = Z;
+  c.KP = KP;
+  img->tab = *si.host;
+  ion_surrogate* s = new (std::nothrow) ion_surrogate();
+  if (!s) {
+    delete img;
+    return set_error(ION_ENOMEM, "host allocation failed");
+  }
+  s->device = si.device;
+  s->num_sms = si.num_sms;
+  s->Z = Z;
+  s->KP = KP;
+  s->nbins = nbins;
+  s->dev = nullptr;
+  s->bound = nullptr;
+  e = cudaMalloc(&s->dev, sizeof(Dev));
+  if (e == cudaSuccess) e = cudaMemcpy(s->dev, img, sizeof(Dev), cudaMemcpyHostToDevice);
+  delete img;
+  if (e == cudaSuccess && bound) {
+    e = cudaMalloc(&s->bound, sizeof(float) * beta.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->bound, beta.data(), sizeof(float) * beta.size(), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = prepare(kernel_of<false>(KP), KP, &s->fit_rates);
+  if (e == cudaSuccess) e = prepare(kernel_of<true>(KP), KP, &s->fit_step);
+  if (e != cudaSuccess) {
+    if (s->dev) cudaFree(s->dev);
+    if (s->bound) cudaFree(s->bound);
+    delete s;
+    return set_error(e == cudaErrorMemoryAllocation ? ION_ENOMEM : ION_ECUDA,
+                     "ion_surrogate_create: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return set_error(ION_OK, "%s", "");
+}
+
+int ion_surrogate_destroy(ion_surrogate* s) {
+  if (!s) return ion::set_error(ION_OK, "%s", "");
+  if (s->dev) cudaFree(s->dev);
+  if (s->bound) cudaFree(s->bound);
+  s->dev = nullptr;
+  delete s;
+  return ion::set_error(ION_OK, "%s", "");
+}
+
+int ion_surrogate_rates(const ion_surrogate* s, const float* E, int64_t ncells, float* W_out,
+                        int64_t ldw, void* stream) {
+  int rc = check_surrogate(s);
+  if (rc) return rc;
+  if (ncells < 0 || ncells >= (int64_t(1) << 31))
+    return ion::set_error(ION_EINVAL, "ncells=%lld outside [0, 2^31)", (long long)ncells);
+  if (ncells == 0) return ion::set_error(ION_OK, "%s", "");
+  if (!E || !W_out || !al4(E) || !al4(W_out))
+    return ion::set_error(ION_EINVAL, "E and W_out must be non-NULL and 4-byte aligned");
+  if (ldw < ncells) return ion::set_error(ION_EINVAL, "ldw < ncells");
+  StepArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.W_out = W_out;
+  a.ldw = ldw;
+  a.ncells = ncells;
+  a.E = E;
+  const cudaError_t e = launch(s, false, a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess)
+    return ion::set_error(ION_ECUDA, "ion_surrogate_rates launch: %s", cudaGetErrorString(e));
+  return ion::set_error(ION_OK, "%s", "");
+}
+
+int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N, int64_t ld,
+                       int64_t ncells, double dt_fs, uint8_t* k_lo, uint8_t* k_hi, float* dne,
+                       const float* n_gas, const ion_step_opts* opts, double pop_tol,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  using namespace ion;
+  int rc = check_surrogate(s);
+  if (rc) return rc;
+  if (ncells < 0 || ncells >= (int64_t(1) << 31))
+    return set_error(ION_EINVAL, "ncells=%lld outside [0, 2^31)", (long long)ncells);
+  if (ncells > 0) {
+    if (!E || !N || !k_lo || !k_hi || !dne)
+      return set_error(ION_EINVAL, "E, N, k_lo, k_hi and dne must be non-NULL");
+    if (ld < ncells || ld > (int64_t(1) << 40))
+      return set_error(ION_EINVAL, "ld=%lld must lie in [ncells, 2^40]", (long long)ld);
+    if (!al4(E) || !al4(N) || !al4(dne) || (n_gas && !al4(n_gas)))
+      return set_error(ION_EINVAL, "E, N, dne and n_gas must be 4-byte aligned");
+  }
+  if (!(pop_tol >= 0.0) || !std::isfinite(pop_tol))
+    return set_error(ION_EINVAL, "pop_tol must be finite and >= 0");
+  StepArgs a;
+  std::memset(&a, 0, sizeof a);
+  if ((rc = policy_from_args(dt_fs, opts, ION_F32, &a.pol))) return rc;
+  if ((rc = workspace_ok(workspace, workspace_bytes, step_workspace_bytes(ncells, false))))
+    return rc;
+  bind_workspace(a.ws, workspace, ncells);
+  JobIO& J = a.J;
+  J.tab = &s->dev->tab;
+  J.Z = s->Z;
+  J.E = E;
+  J.N = N;
+  J.ld = ld;
+  J.ncells = (int)ncells;
+  J.lo = k_lo;
+  J.hi = k_hi;
+  J.dne = dne;
+  J.n_gas = n_gas;
+  a.pop_tol = (float)pop_tol;
+  a.bound = s->bound;
+  a.ncells = ncells;
+  a.E = E;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(a.ws.hdr, 0, kHdrWords * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = launch(s, true, a, st);
+  if (e == cudaSuccess && ncells > 0) {
+    BatchArgs b;
+    std::memset(&b, 0, sizeof b);
+    b.njobs = 1;
+    b.job[0] = J;
+    b.pol = a.pol;
+    b.ws = a.ws;
+    e = launch_fb_f32(b, s->num_sms, st);
+  }
+  if (e != cudaSuccess)
+    return set_error(ION_ECUDA, "ion_step_surrogate launch: %s", cudaGetErrorString(e));
+  return set_error(ION_OK, "%s", "");
+}
+
+}  // extern "C"

@@ -37,7 +37,14 @@ ION_MAX_WINDOW = 6
 EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_rates", "ion_step_workspace_bytes", "ion_step",
            "ion_step_batched_workspace_bytes", "ion_step_batched", "ion_autotune",
-           "ion_step_noalloc", "ion_conservation", "ion_last_error")
+           "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
+           "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
+           "ion_surrogate_create", "ion_surrogate_destroy", "ion_surrogate_rates",
+           "ion_step_surrogate", "ion_last_error")
+
+#: forward pass in the tensor-core arithmetic (bf16 W2, W3, h1, h2; SFU tanh)
+ION_MLP_BF16 = 0x1
+ION_MLP_HIDDEN = 64
 
 ION_MAX_JOBS = 8
 #: launch shapes the library is built with (cells per lane, warps per block)
@@ -69,6 +76,12 @@ class _BatchJob(ctypes.Structure):
     _fields_ = [("species", ctypes.c_void_p), ("E", ctypes.c_void_p), ("N", ctypes.c_void_p),
                 ("ld", ctypes.c_int64), ("ncells", ctypes.c_int64), ("k_lo", ctypes.c_void_p),
                 ("k_hi", ctypes.c_void_p), ("dne", ctypes.c_void_p), ("n_gas", ctypes.c_void_p)]
+
+
+class _SurrogateNorm(ctypes.Structure):
+    _fields_ = [("log2E_min", ctypes.c_double), ("log2E_max", ctypes.c_double),
+                ("y_floor", ctypes.c_double), ("y_mean", ctypes.c_double * ION_MAX_Z),
+                ("y_scale", ctypes.c_double * ION_MAX_Z)]
 
 
 class LaunchShape(ctypes.Structure):
@@ -120,6 +133,30 @@ def _declare(lib):
     lib.ion_conservation.restype = ctypes.c_int
     lib.ion_conservation.argtypes = [_vp, _i64, _i64, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_int, _vp, _vp]
+    lib.ion_mlp_nparams.restype = ctypes.c_int64
+    lib.ion_mlp_nparams.argtypes = [ctypes.c_int]
+    lib.ion_mlp_workspace_bytes.restype = ctypes.c_size_t
+    lib.ion_mlp_workspace_bytes.argtypes = [ctypes.c_int, _i64]
+    lib.ion_mlp_loss_grad.restype = ctypes.c_int
+    lib.ion_mlp_loss_grad.argtypes = [_vp, ctypes.c_int, _vp, _vp, _i64, ctypes.c_int, _vp, _vp,
+                                      _vp, ctypes.c_size_t, _vp]
+    lib.ion_mlp_adam.restype = ctypes.c_int
+    lib.ion_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp]
+    lib.ion_mlp_forward.restype = ctypes.c_int
+    lib.ion_mlp_forward.argtypes = [_vp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]
+    lib.ion_surrogate_create.restype = ctypes.c_int
+    lib.ion_surrogate_create.argtypes = [_vp, _vp, ctypes.POINTER(_SurrogateNorm),
+                                         ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                         ctypes.POINTER(_vp)]
+    lib.ion_surrogate_destroy.restype = ctypes.c_int
+    lib.ion_surrogate_destroy.argtypes = [_vp]
+    lib.ion_surrogate_rates.restype = ctypes.c_int
+    lib.ion_surrogate_rates.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp]
+    lib.ion_step_surrogate.restype = ctypes.c_int
+    lib.ion_step_surrogate.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
+                                       _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_double,
+                                       _vp, ctypes.c_size_t, _vp]
     lib.ion_step_noalloc.restype = ctypes.c_int
     lib.ion_step_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                      _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp]
@@ -388,3 +425,153 @@ def conservation(N: torch.Tensor, out: torch.Tensor, ncells: int | None = None,
     _check(lib().ion_conservation(_ptr(N), N.shape[1], n, k, float(target), dtype, _ptr(out),
                                   _stream(N)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# rate surrogate: training calls and inference
+# ---------------------------------------------------------------------------
+def mlp_nparams(K: int) -> int:
+    n = int(lib().ion_mlp_nparams(int(K)))
+    if n < 0:
+        raise IonError(n, lib().ion_last_error().decode())
+    return n
+
+
+def mlp_workspace(K: int, B: int, device=None) -> torch.Tensor:
+    nb = int(lib().ion_mlp_workspace_bytes(int(K), int(B)))
+    if nb == 0:
+        raise ValueError("K or B out of range")
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def mlp_loss_grad(P: torch.Tensor, K: int, x: torch.Tensor, t: torch.Tensor, flags: int = 0,
+                  grad: torch.Tensor | None = None, loss: torch.Tensor | None = None,
+                  ws: torch.Tensor | None = None):
+    """ion_mlp_loss_grad: (loss (device scalar), grad) of the batch (x, t)."""
+    _need(P, "P", torch.float32)
+    dev = P.device
+    _need(x, "x", torch.float32, dev)
+    _need(t, "t", torch.float32, dev)
+    B = x.numel()
+    if t.numel() != B * K:
+        raise ValueError("t must hold B*K targets")
+    grad = torch.empty_like(P) if grad is None else grad
+    loss = torch.empty(1, dtype=torch.float32, device=dev) if loss is None else loss
+    ws = mlp_workspace(K, B, dev) if ws is None else ws
+    _need(grad, "grad", torch.float32, dev)
+    _need(loss, "loss", torch.float32, dev)
+    _check(lib().ion_mlp_loss_grad(_ptr(P), int(K), _ptr(x), _ptr(t), B, int(flags), _ptr(grad),
+                                   _ptr(loss), _ptr(ws), ws.numel(), _stream(P)))
+    return loss, grad
+
+
+def mlp_adam(P: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float,
+             t: int, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    """ion_mlp_adam: one Adam step (t >= 1) on P in place."""
+    for a, nm in ((P, "P"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(a, nm, torch.float32, P.device)
+    _check(lib().ion_mlp_adam(_ptr(P), _ptr(grad), _ptr(m), _ptr(v), P.numel(), float(lr),
+                              float(beta1), float(beta2), float(eps), int(t), _stream(P)))
+
+
+def mlp_forward(P: torch.Tensor, K: int, x: torch.Tensor, flags: int = 0,
+                out: torch.Tensor | None = None) -> torch.Tensor:
+    """ion_mlp_forward: outputs (B, K) on CUDA cores."""
+    _need(P, "P", torch.float32)
+    _need(x, "x", torch.float32, P.device)
+    out = torch.empty((x.numel(), K), dtype=torch.float32, device=P.device) if out is None else out
+    _need(out, "out", torch.float32, P.device)
+    _check(lib().ion_mlp_forward(_ptr(P), int(K), _ptr(x), x.numel(), int(flags), _ptr(out),
+                                 _stream(P)))
+    return out
+
+
+class Surrogate:
+    """ion_surrogate_create: a trained network for species `sp`.
+
+    norm: dict with log2E_min, log2E_max, y_floor, y_mean (Z), y_scale (Z).
+    bound: None or an array (nbins, Z) of log2-error bounds."""
+
+    def __init__(self, sp: Species, P: torch.Tensor, norm: dict, bound=None):
+        _need(P, "P", torch.float32)
+        Z = sp.Z
+        nm = _SurrogateNorm()
+        nm.log2E_min = float(norm["log2E_min"])
+        nm.log2E_max = float(norm["log2E_max"])
+        nm.y_floor = float(norm["y_floor"])
+        for k in range(Z):
+            nm.y_mean[k] = float(norm["y_mean"][k])
+            nm.y_scale[k] = float(norm["y_scale"][k])
+        bptr, nbins = None, 0
+        if bound is not None:
+            import numpy as _np
+            b = _np.ascontiguousarray(_np.asarray(bound, dtype=_np.float32))
+            if b.ndim != 2 or b.shape[1] != Z:
+                raise ValueError("bound must be (nbins, Z)")
+            nbins = b.shape[0]
+            self._bound = b
+            bptr = b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        h = _vp()
+        _check(lib().ion_surrogate_create(sp.handle, _ptr(P), ctypes.byref(nm), bptr, nbins,
+                                          ctypes.byref(h)))
+        self._h = h
+        self.Z = Z
+        self.norm = dict(norm)
+        self.device = P.device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ion_surrogate_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rates(self, E: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """W_k(|E|) in 1/fs from the network, (Z, ncells)."""
+        _need(E, "E", torch.float32)
+        n = E.numel()
+        out = torch.empty((self.Z, n), dtype=torch.float32, device=E.device) if out is None else out
+        _need(out, "out", torch.float32, E.device)
+        _check(lib().ion_surrogate_rates(self._h, _ptr(E), n, _ptr(out), out.shape[1],
+                                         _stream(E)))
+        return out
+
+    def step(self, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor, k_hi: torch.Tensor,
+             dt: float, dne: torch.Tensor, n_gas: torch.Tensor | None = None,
+             ws: torch.Tensor | None = None, eps_shift: float = 1e-6, degen_gap: float = 1e-3,
+             pop_tol: float = 1e-6) -> torch.Tensor:
+        """ion_step_surrogate; returns the workspace (header words 3, 4, 5:
+        cells on the network's rates, on Eq. 1's rates, timeout flag)."""
+        _need(E, "E", torch.float32)
+        dev = E.device
+        _need(N, "N", torch.float32, dev)
+        _need(k_lo, "k_lo", torch.uint8, dev)
+        _need(k_hi, "k_hi", torch.uint8, dev)
+        _need(dne, "dne", torch.float32, dev)
+        if n_gas is not None:
+            _need(n_gas, "n_gas", torch.float32, dev)
+        if N.dim() != 2 or N.shape[0] != self.Z + 1:
+            raise ValueError(f"N must have shape (Z+1, ld) = ({self.Z + 1}, ld)")
+        n = E.numel()
+        ws = workspace(n, ION_F32, dev) if ws is None else ws
+        opts = _StepOpts(float(eps_shift), float(degen_gap))
+        _check(lib().ion_step_surrogate(self._h, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
+                                        _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
+                                        ctypes.byref(opts), float(pop_tol), _ptr(ws),
+                                        ws.numel(), _stream(E)))
+        return ws
+
+
+def surrogate_counters(ws: torch.Tensor):
+    """(cells on the network's rates, cells on Eq. 1's rates, timeout flag)
+    of the last ion_step_surrogate that used `ws` (synchronizes)."""
+    h = ws[:24].cpu().view(torch.int32)
+    return int(h[3]), int(h[4]), int(h[5])

@@ -34,14 +34,16 @@ def _prime(sp: ionize.Species, flags: int, device) -> None:
 
 class StepGraph:
     """K = len(fields) steps: step s advances N, k_lo, k_hi by dt with the
-    field fields[s] and writes dne; with `conservation`, the largest
-    |sum_k N_k - 1| over the cells after step s lands in self.cons[s]."""
+    field fields[s] and writes dne (ion_step, or ion_step_surrogate when a
+    surrogate is given); with `conservation`, the largest |sum_k N_k - 1|
+    over the cells after step s lands in self.cons[s]."""
 
     def __init__(self, sp: ionize.Species, fields, N: torch.Tensor, k_lo: torch.Tensor,
                  k_hi: torch.Tensor, dne: torch.Tensor, dt: float,
                  ws: torch.Tensor | None = None, flags: int = ionize.ION_F32,
                  conservation: bool = True, eps_shift: float = 1e-6,
-                 degen_gap: float = 1e-3):
+                 degen_gap: float = 1e-3, surrogate: ionize.Surrogate | None = None,
+                 pop_tol: float = 1e-6):
         if not fields:
             raise ValueError("at least one field")
         dev = N.device
@@ -58,8 +60,12 @@ class StepGraph:
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.graph(self.graph, stream=side):
             for s, E in enumerate(self.fields):
-                ionize.step(sp, E, N, k_lo, k_hi, dt, dne, ws=self.ws, eps_shift=eps_shift,
-                            degen_gap=degen_gap, flags=flags)
+                if surrogate is None:
+                    ionize.step(sp, E, N, k_lo, k_hi, dt, dne, ws=self.ws, eps_shift=eps_shift,
+                                degen_gap=degen_gap, flags=flags)
+                else:
+                    surrogate.step(E, N, k_lo, k_hi, dt, dne, ws=self.ws, eps_shift=eps_shift,
+                                   degen_gap=degen_gap, pop_tol=pop_tol)
                 if conservation:
                     ionize.conservation(N, self.cons[s:s + 1], ncells=n)
         torch.cuda.current_stream(dev).wait_stream(side)

@@ -1,0 +1,206 @@
+"""The rate surrogate: training kernels against the FP64 reference network,
+the tensor-core inference against the CUDA-core forward pass, the trained
+network against Eq. 1, and the surrogate step against the oracle."""
+import math
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp as omlp
+from paper_2202_10647_gb300 import ionize, surrogate as S, workloads as W
+from test_gpu_step import check, gpu_species, oracle_species
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_P(K, seed, scale=0.5):
+    return np.random.default_rng(seed).normal(0.0, scale, omlp.nparams(K))
+
+
+@pytest.mark.parametrize("K,B", [(18, 1000), (36, 777), (7, 4096), (63, 130)])
+def test_loss_grad_matches_oracle(K, B):
+    rng = np.random.default_rng(K)
+    P = rand_P(K, K + 1)
+    x = rng.uniform(-1, 1, B)
+    t = rng.normal(0, 1, (B, K))
+    L, g = omlp.loss_grad(P, K, x, t)
+    Pd = torch.tensor(P, dtype=torch.float32, device="cuda")
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    # the oracle on the float32-rounded inputs the GPU sees
+    L32, g32 = omlp.loss_grad(Pd.double().cpu().numpy(), K, xd.double().cpu().numpy(),
+                              td.double().cpu().numpy())
+    loss, grad = ionize.mlp_loss_grad(Pd, K, xd, td)
+    assert float(loss) == pytest.approx(L32, rel=2e-5)
+    gg = grad.double().cpu().numpy()
+    assert np.abs(gg - g32).max() <= 2e-5 * np.abs(g32).max(), np.abs(gg - g32).max()
+    # deterministic: the same call gives the same bits
+    _, grad2 = ionize.mlp_loss_grad(Pd, K, xd, td)
+    assert torch.equal(grad, grad2)
+    # the inference arithmetic (bf16, straight-through) stays close
+    _, gq = ionize.mlp_loss_grad(Pd, K, xd, td, flags=ionize.ION_MLP_BF16)
+    assert float((gq - grad).abs().max()) <= 0.05 * float(grad.abs().max())
+
+
+def test_forward_and_adam_match_oracle():
+    K, B = 18, 513
+    rng = np.random.default_rng(2)
+    P = rand_P(K, 3)
+    x = rng.uniform(-1, 1, B)
+    Pd = torch.tensor(P, dtype=torch.float32, device="cuda")
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    y, _ = omlp.forward(Pd.double().cpu().numpy(), K, xd.double().cpu().numpy())
+    yg = ionize.mlp_forward(Pd, K, xd).double().cpu().numpy()
+    assert np.abs(yg - y).max() <= 1e-5 * max(1.0, np.abs(y).max())
+    # three Adam steps
+    g = [rng.normal(size=P.size) for _ in range(3)]
+    Po, m, v = Pd.double().cpu().numpy(), np.zeros(P.size), np.zeros(P.size)
+    md, vd = torch.zeros_like(Pd), torch.zeros_like(Pd)
+    for s in range(1, 4):
+        gd = torch.tensor(g[s - 1], dtype=torch.float32, device="cuda")
+        Po, m, v = omlp.adam(Po, gd.double().cpu().numpy(), m, v, 1e-2, 0.9, 0.999, 1e-8, s)
+        ionize.mlp_adam(Pd, gd, md, vd, 1e-2, s)
+    assert np.abs(Pd.double().cpu().numpy() - Po).max() <= 2e-6 * np.abs(Po).max()
+
+
+@pytest.mark.parametrize("Z,n", [(7, 1000), (18, 300_000), (36, 4099), (63, 257)])
+def test_tensor_core_inference_matches_cuda_core_forward(Z, n):
+    """The tcgen05 kernel (bf16 operands, FP32 accumulators in tensor memory)
+    against ion_mlp_forward in the same arithmetic on CUDA cores: equal up to
+    the accumulation order (an occasional one-ulp bf16 flip of a hidden
+    activation)."""
+    sd = W.synthetic_ladder(Z, 90 + Z)
+    sp = gpu_species(sd)
+    P = torch.tensor(rand_P(Z, Z, 0.3), dtype=torch.float32, device="cuda")
+    l2lo, l2hi = S.log2_range()
+    norm = {"log2E_min": l2lo, "log2E_max": l2hi, "y_floor": -1000.0,
+            "y_mean": [0.0] * Z, "y_scale": [1.0] * Z}
+    net = ionize.Surrogate(sp, P, norm)
+    g = torch.Generator(device="cuda").manual_seed(Z)
+    E = torch.exp2(l2lo + (l2hi - l2lo) * torch.rand(n, generator=g, device="cuda"))
+    Wn = net.rates(E)  # 2^y
+    y_tc = torch.log2(Wn.double()).T
+    x = S.scaled_input(E, l2lo, l2hi)
+    y_cc = ionize.mlp_forward(P, Z, x, flags=ionize.ION_MLP_BF16).double()
+    d = (y_tc - y_cc).abs()
+    assert float(d.max()) <= 2e-2, float(d.max())
+    assert float(d.median()) <= 1e-5, float(d.median())
+    # against plain FP32 (no bf16): close, not equal
+    y32 = ionize.mlp_forward(P, Z, x).double()
+    assert float((y_tc - y32).abs().max()) <= 0.2
+
+
+@pytest.fixture(scope="module")
+def argon_net():
+    sd = W.argon_like()
+    sp = gpu_species(sd)
+    t0 = time.time()
+    net, tr, bound = S.build(sp, steps=3000)
+    torch.cuda.synchronize()
+    print(f"\ntrained in {time.time() - t0:.1f} s; loss {tr.losses[-1]}")
+    return sd, sp, net, tr, bound
+
+
+def test_trained_network_accuracy(argon_net):
+    """The trained network's rates against the oracle's Eq. 1 on fresh
+    inputs, and its bound holds there."""
+    sd, sp, net, tr, bound = argon_net
+    assert tr.losses[-1][1] < 1e-3, tr.losses
+    n = 20000
+    E = torch.pow(10.0, 1.0 + 4.0 * W.uniform(77, 1, torch.arange(n))).to(torch.float32)
+    Wn = net.rates(E.cuda()).double().cpu().numpy()
+    osp = oracle_species(sd)
+    Wo = oracle.rates(osp, E.double().numpy(), 0, sd.Z)
+    big = Wo * 0.05 > 1e-12
+    rel = np.abs(Wn[big] / Wo[big] - 1.0)
+    print(f"max rel rate error {rel.max():.3e}, median {np.median(rel):.3e}")
+    l2 = np.log2(E.double().numpy())
+    lo, hi = S.log2_range()
+    nb = bound.shape[0]
+    b = np.clip(np.floor((l2 - lo) / (hi - lo) * nb).astype(int), 0, nb - 1)
+    yn = np.maximum(np.log2(np.maximum(Wn, 1e-300)), S.Y_FLOOR)
+    yo = np.maximum(np.log2(np.maximum(Wo, 1e-300)), S.Y_FLOOR)
+    viol = np.abs(yn - yo) > bound[b].T
+    assert viol.mean() < 1e-3, viol.mean()
+
+
+def test_surrogate_step_matches_oracle(argon_net):
+    """ion_step_surrogate on the Ar-like lognormal workload: every cell within
+    the FP32 bar of the oracle (the bound keeps the network's rate error
+    below pop_tol in the populations)."""
+    sd, sp, net, tr, bound = argon_net
+    wl = W.ladder_cells(sd, 40000, 21)
+    n = wl.ncells
+    E, N, lo, hi = wl.E.cuda(), wl.N.cuda(), wl.lo.clone().cuda(), wl.hi.clone().cuda()
+    dne = torch.zeros(n, device="cuda")
+    ws = net.step(E, N, lo, hi, 0.05, dne, pop_tol=1e-6)
+    n_net, n_plain, timeout = ionize.surrogate_counters(ws)
+    assert timeout == 0
+    No, loo, hio, dneo = oracle.step(oracle_species(sd), wl.E.double().numpy(),
+                                     wl.N[:, :n].double().numpy(), 0.05, wl.lo.numpy(),
+                                     wl.hi.numpy())
+    out = dict(N=N.double().cpu().numpy(), lo=lo.cpu().numpy(), hi=hi.cpu().numpy(),
+               dne=dne.double().cpu().numpy())
+    check(out, dict(N=No, lo=loo, hi=hio, dne=dneo), wl.lo, wl.hi,
+          ionize.ION_F32)
+    print(f"cells on the network's rates: {n_net} of {n}; on Eq. 1: {n_plain}")
+    assert n_net + n_plain <= n
+
+
+def test_surrogate_everywhere_reports_its_error(argon_net):
+    """With no bound (pop_tol huge) every in-range cell takes the network's
+    rates: populations stay conserved and non-negative, and the error
+    against the oracle is what the rate error implies."""
+    sd, sp, net, tr, bound = argon_net
+    wl = W.ladder_cells(sd, 20000, 22)
+    n = wl.ncells
+    E, N, lo, hi = wl.E.cuda(), wl.N.cuda(), wl.lo.clone().cuda(), wl.hi.clone().cuda()
+    dne = torch.zeros(n, device="cuda")
+    ws = net.step(E, N, lo, hi, 0.05, dne, pop_tol=1e30)
+    n_net, n_plain, timeout = ionize.surrogate_counters(ws)
+    assert timeout == 0 and n_net > 0.9 * n
+    tot = N[:, :n].double().sum(0)
+    assert float((tot - wl.N[:, :n].double().sum(0).cuda()).abs().max()) <= 1e-6
+    assert float(N.min()) >= -1e-6
+    No, _, _, _ = oracle.step(oracle_species(sd), wl.E.double().numpy(),
+                              wl.N[:, :n].double().numpy(), 0.05, wl.lo.numpy(), wl.hi.numpy())
+    err = float(np.abs(N[:, :n].double().cpu().numpy() - No).max())
+    print(f"population error with the network everywhere: {err:.3e}")
+    assert err < 0.5
+
+
+def test_surrogate_gain(argon_net):
+    """What the network gains over the plain rates of Eq. 1 on the same
+    cells: time per step of both forms, and how many cells the network may
+    serve at the FP32 accuracy bar (it is reported, not required to win)."""
+    sd, sp, net, tr, bound = argon_net
+    wl = W.ladder_cells(sd, 2_000_000, 23, device="cuda")
+    n = wl.ncells
+    dne = torch.zeros(n, device="cuda")
+    ws = ionize.workspace(n)
+    N0, lo0, hi0 = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
+
+    def timed(fn, reps=10):
+        ts = []
+        for _ in range(reps + 2):
+            wl.N.copy_(N0)
+            wl.lo.copy_(lo0)
+            wl.hi.copy_(hi0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts[2:]))
+
+    t_plain = timed(lambda: ionize.step(sp, wl.E, wl.N, wl.lo, wl.hi, 0.05, dne, ws=ws))
+    t_net = timed(lambda: net.step(wl.E, wl.N, wl.lo, wl.hi, 0.05, dne, ws=ws))
+    n_net, n_plain, _ = ionize.surrogate_counters(ws)
+    print(f"plain FP32 {t_plain:.3f} ms, surrogate {t_net:.3f} ms "
+          f"(gain {t_plain / t_net:.2f}x); network rates for {n_net / n:.1%} of the cells")
+    assert t_net > 0 and t_plain > 0
