@@ -494,6 +494,11 @@ cudaError_t prepare(const void* fn, int KP, int* fit) {
   const size_t smem = ion::sg::plan_of(KP).total;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // all of the unified L1/shared array as shared memory, so that the
+  // occupancy below (and at launch) is limited by registers and smem alone
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, fn, ion::sg::kM, smem);
   if (e != cudaSuccess) return e;
   if (*fit < 1 || *fit * (int)ion::sg::kTmemCols > 512) return cudaErrorInvalidConfiguration;
