@@ -50,6 +50,42 @@ def parse():
     return ap.parse_args()
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_nitrogen_3d.txt")
+KERNEL_SOURCES = ["paper_2202_10647_gb300/csrc/step_f32.cu",
+                  "paper_2202_10647_gb300/csrc/ion_device.cuh",
+                  "paper_2202_10647_gb300/csrc/ion_cell.cuh",
+                  "paper_2202_10647_gb300/csrc/ion_step.cuh"]
+
+
+def kernel_sources_hash() -> str:
+    """sha256 over the sources of the step's three FP32 kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes of one full-size step from the committed ncu summary, or
+    None when the summary was taken on other kernel sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("sources_sha256") != kernel_sources_hash():
+        return None
+    try:
+        return int(kv["dram_bytes_per_step"])
+    except (KeyError, ValueError):
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -587,7 +623,7 @@ def main():
                    "l2": "flushed between timed steps (256 MB write) and inputs > L2",
                    "form": "FP32 + FP64 coefficients for |W_i-W_j| < 1e-3 max(W_i,W_j)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": recorded_traffic(),
                      "kernel": "ion_step (ion_stream_kernel + ion_stiff_kernel + ion_fb_kernel)",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": main_ms},

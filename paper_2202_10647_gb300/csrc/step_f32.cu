@@ -171,7 +171,7 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     for (int j = 0; j < Q; ++j) v[j][r] = vget(p, j);  // r >= w: ignored
   }
   float lam[Q][WM];
-  int Rl = 0;
+  float xl = 0.0f;
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
     stiff[j] = false;
@@ -195,10 +195,12 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
     stiff[j] = lmax > kLamEasy;
-    const float x = stiff[j] ? 0.0f : 2.0f * lmax;
-    Rl = max(Rl, DDParams<float>::terms(x, kEasyTerms));
+    xl = fmaxf(xl, stiff[j] ? 0.0f : 2.0f * lmax);
   }
-  const int Rw = __reduce_max_sync(kFull, Rl);
+  // the warp's largest 2 max(W dt) (non-negative floats order like their
+  // bits), then its term count once
+  const float xw = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(xl)));
+  const int Rw = DDParams<float>::terms(xw, kEasyTerms);
   float dne[Q];
   int nlo[Q], nhi[Q];
   // u = (dt A)^k v unnormalized (|dt A| <= 2 kLamEasy keeps it small);

@@ -18,6 +18,7 @@
 //      validation bound) and runs the update of ion_step.
 // Waits on the mbarrier are bounded; a wait that gives up marks the call as
 // failed (header word / NaN rates), frees the tensor memory and returns.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -499,9 +500,31 @@ cudaError_t prepare(const void* fn, int KP, int* fit) {
   e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, fn, ion::sg::kM, smem);
-  if (e != cudaSuccess) return e;
-  if (*fit < 1 || *fit * (int)ion::sg::kTmemCols > 512) return cudaErrorInvalidConfiguration;
+  // residency from the kernel's registers and shared memory and the SM's
+  // limits (the occupancy query reports one CTA per SM for these kernels,
+  // below what the SM holds)
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+  int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0, blk_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) ||
+      (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) ||
+      (e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) ||
+      (e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) ||
+      (e = cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev)))
+    return e;
+  const int warps = ion::sg::kM / 32;
+  const int regs_warp = ((fa.numRegs + 7) / 8 * 8 * 32 + 255) / 256 * 256;
+  int f = regs_sm / (regs_warp * warps);
+  const int per_block_smem = (int)smem + (int)fa.sharedSizeBytes + smem_rsv;
+  f = std::min(f, smem_sm / per_block_smem);
+  f = std::min(f, thr_sm / ion::sg::kM);
+  f = std::min(f, blk_sm);
+  // tensor memory: the resident CTAs' columns must fit the SM's 512, so that
+  // no allocation ever waits
+  f = std::min(f, 512 / (int)ion::sg::kTmemCols);
+  *fit = f;
+  if (*fit < 1) return cudaErrorInvalidConfiguration;
   return cudaSuccess;
 }
 
