@@ -383,9 +383,12 @@ ION_API int ion_surrogate_rates(const ion_surrogate* s, const float* E, int64_t 
  *   2 dt sum_r (max(W_r, 2^y_floor) (2^bound - 1) + 2^y_floor)
  * (a perturbation of the rate matrix by dA moves the solution of Eq. 3 by
  * at most |dA| in the 1-norm); if it is at most pop_tol the network's rates
- * are used, otherwise (and outside the range) the rates of Eq. 1.  The
- * update itself is ion_step's (Taylor or Bateman form, FP64 coefficients for
- * nearly degenerate rate pairs, window slide).  Arguments as ion_step with
+ * are used, otherwise (and outside the range) the rates of Eq. 1.  A cell
+ * with some rate W dt > 1 always takes the rates of Eq. 1 (its bound would
+ * exceed any useful tolerance) and is finished in the Bateman form by
+ * ion_step's record kernel.  The update itself is ion_step's (Taylor or
+ * Bateman form, FP64 coefficients for nearly degenerate rate pairs, window
+ * slide).  Arguments as ion_step with
  * FP32 arrays; pop_tol >= 0.  Workspace: ion_step_workspace_bytes(ncells,
  * ION_F32); after the call its header holds, besides the words described
  * for ion_step, word 3: cells that took the network's rates, word 4: cells

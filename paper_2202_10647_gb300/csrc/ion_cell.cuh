@@ -80,6 +80,30 @@ __device__ __forceinline__ void warp_append(uint32_t* counter, uint32_t* queue,
   }
 }
 
+// Appends the record of a stiff cell (one atomic per warp).  Every lane of
+// the warp calls this; `take` lanes pass their cell's inputs.
+__device__ __forceinline__ void append_record(const Scratch& S, bool take, int job,
+                                              int c, float Ec, int lo, int hi,
+                                              const float* v) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(&S.hdr[kHdrStiff], (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, 0);
+  if (take) {
+    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
+    S.rec_c[i] = (uint32_t)c;
+    S.rec_job[i] = (uint8_t)job;
+    S.rec_E[i] = Ec;
+    S.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
+    const int w = hi - lo + 1;
+#pragma unroll
+    for (int r = 0; r < ION_MAX_WINDOW; ++r)
+      if (r < w) S.rec_V[(int64_t)r * S.rec_cap + i] = v[r];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Update of one cell whose window populations v[0..w-1] and rates
 // lam[r] = W_{lo+r} dt (r < w-1; 0 beyond) are known (2 <= w <= WM): Taylor

@@ -104,8 +104,9 @@ int workspace_ok(void* workspace, size_t have, size_t need);
 // and `a.nchunks` are filled in by launch_batch_f32.
 cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms,
                              cudaStream_t s);
-// The FP64-coefficient pass over the cells queued by a previous kernel of the
-// same call (step_f32.cu).
+// The stiff-cell records and the FP64-coefficient queue left by a previous
+// kernel of the same call (step_f32.cu).
+cudaError_t launch_stiff_f32(const BatchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_fb_f32(const BatchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_step_f64(const JobIO& job, const Policy& pol, uint32_t* hdr,
                             cudaStream_t s);

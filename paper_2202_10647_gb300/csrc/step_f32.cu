@@ -121,30 +121,6 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
   return j;
 }
 
-// Appends the record of a stiff cell (one atomic per warp).  Every lane of
-// the warp calls this; `take` lanes pass their cell's inputs.
-__device__ __forceinline__ void append_record(const Scratch& S, bool take, int job,
-                                              int c, float Ec, int lo, int hi,
-                                              const float* v) {
-  const unsigned m = __ballot_sync(kFull, take);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  unsigned base = 0;
-  if (lane == 0) base = atomicAdd(&S.hdr[kHdrStiff], (unsigned)__popc(m));
-  base = __shfl_sync(kFull, base, 0);
-  if (take) {
-    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
-    S.rec_c[i] = (uint32_t)c;
-    S.rec_job[i] = (uint8_t)job;
-    S.rec_E[i] = Ec;
-    S.rec_lohi[i] = (uint16_t)(lo | (hi << 8));
-    const int w = hi - lo + 1;
-#pragma unroll
-    for (int r = 0; r < ION_MAX_WINDOW; ++r)
-      if (r < w) S.rec_V[(int64_t)r * S.rec_cap + i] = v[r];
-  }
-}
-
 // Easy path of the lane's Q cells (c0..c0+Q-1 of job J, window bound WM).
 // Every lane of the warp calls this.  Cells whose rates all have
 // W dt <= kLamEasy are finished; stiff[j] marks the others, left untouched.
@@ -765,9 +741,13 @@ cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms
   if (blocks < 1) blocks = 1;  // the tails still need a warp
   void* args[] = {&a};
   if ((e = cudaLaunchKernel(v->fn, blocks, v->W * 32, args, smem, s)) != cudaSuccess) return e;
-  ion_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_stiff_f32(a, num_sms, s)) != cudaSuccess) return e;
   return launch_fb_f32(a, num_sms, s);
+}
+
+cudaError_t launch_stiff_f32(const BatchArgs& a, int num_sms, cudaStream_t s) {
+  ion_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fb_f32(const BatchArgs& a, int num_sms, cudaStream_t s) {

@@ -13,9 +13,12 @@
 //      reusing the same accumulator columns;
 //   5. the outputs, scaled to log2 W, are staged column-major in shared
 //      memory (conflict-free for any window position), and each thread
-//      finishes its cell: ion_surrogate_rates writes all Z rates,
+//      finishes its cell: ion_surrogate_rates writes all Z rates;
 //      ion_step_surrogate picks the window's rates (network or Eq. 1, by the
-//      validation bound) and runs the update of ion_step.
+//      validation bound) and finishes cells whose rates all have W dt <= 1
+//      with the Taylor form.  Cells with a larger rate become records for
+//      ion_step's record kernel (Bateman form, rates of Eq. 1), followed by
+//      its FP64-coefficient pass.
 // Waits on the mbarrier are bounded; a wait that gives up marks the call as
 // failed (header word / NaN rates), frees the tensor memory and returns.
 #include <algorithm>
@@ -185,19 +188,40 @@ struct StepArgs {
   const float* E;
 };
 
-template <int W>
-__device__ __forceinline__ bool step_cell(const StepArgs& a, int c, int lo, int hi,
-                                          const float (&lam6)[ION_MAX_WINDOW]) {
-  const float* __restrict__ N = static_cast<const float*>(a.J.N);
-  float v[W], lam[W];
-  const float* p = N + (int64_t)lo * a.J.ld + c;
+// Taylor-form update of one cell whose rates all have W dt <= 1 (w <= 6,
+// the window's populations loaded here): the same series, window slide and
+// stores as ion_step's streaming kernel.
+__device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, int hi,
+                                            const float (&lam)[ION_MAX_WINDOW], float lmax) {
+  const JobIO& J = a.J;
+  float* __restrict__ N = static_cast<float*>(J.N);
+  const int w = hi - lo + 1;
+  float dne = 0.0f;
+  int nlo = lo, nhi = hi;
+  if (w >= 2) {
+    float v[ION_MAX_WINDOW];
+    const float* p = N + (int64_t)lo * J.ld + c;
 #pragma unroll
-  for (int r = 0; r < W; ++r) {
-    v[r] = __ldcs(p);
-    p += a.J.ld;
-    lam[r] = lam6[r];
+    for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+      v[r] = r < w ? __ldcs(p) : 0.0f;
+      p += J.ld;
+    }
+    dne = taylor_propagate<float, ION_MAX_WINDOW>(v, lam, w, lmax);
+    if ((a.pol.flags & ION_NO_WINDOW_UPDATE) == 0)
+      slide_window<float, ION_MAX_WINDOW>(v, w, J.Z, (float)a.pol.eps, nlo, nhi);
+    float* q = N + (int64_t)lo * J.ld + c;
+#pragma unroll
+    for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+      if (r < w) __stcs(q, v[r]);
+      q += J.ld;
+    }
   }
-  return update_cell<float, W>(a.J, a.pol, c, lo, hi, v, lam, true);
+  const float* __restrict__ G = static_cast<const float*>(J.n_gas);
+  __stcs(static_cast<float*>(J.dne) + c, G ? dne * G[c] : dne);
+  if (nlo != lo) {
+    J.lo[c] = (uint8_t)nlo;
+    J.hi[c] = (uint8_t)nhi;
+  }
 }
 
 // Counts the lanes with `take` set into *counter (one atomic per warp).
@@ -403,32 +427,28 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
             if (r < w - 1) lam[r] = rate_dt_f32(tab, lo + r, f);
         }
       }
+      // cells with some W dt > 1 take the Bateman form in the record kernel,
+      // with the rates of Eq. 1 (their error bound is far above any useful
+      // tolerance, so the network could not serve them)
+      float lmax = 0.0f;
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r) lmax = fmaxf(lmax, lam[r]);
+      const bool stiff = valid && lmax > DDParams<float>::prop_max;
+      net = net && !stiff;
+      plain = plain || stiff;
       warp_count(&a.ws.hdr[kHdrSurrogate], net);
       warp_count(&a.ws.hdr[kHdrPlain], plain);
-      bool fb = false;
-      if (valid) {
-        switch (w) {
-          case 1:
-            fb = step_cell<1>(a, (int)c, lo, hi, lam);
-            break;
-          case 2:
-            fb = step_cell<2>(a, (int)c, lo, hi, lam);
-            break;
-          case 3:
-            fb = step_cell<3>(a, (int)c, lo, hi, lam);
-            break;
-          case 4:
-            fb = step_cell<4>(a, (int)c, lo, hi, lam);
-            break;
-          case 5:
-            fb = step_cell<5>(a, (int)c, lo, hi, lam);
-            break;
-          default:
-            fb = step_cell<6>(a, (int)c, lo, hi, lam);
-            break;
+      if (__ballot_sync(kFull, stiff)) {
+        float vin[ION_MAX_WINDOW];
+        const float* p = static_cast<const float*>(J.N) + (int64_t)lo * J.ld + c;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+          vin[r] = (stiff && r < w) ? __ldcs(p) : 0.0f;
+          p += J.ld;
         }
+        append_record(a.ws, stiff, 0, (int)c, on ? a.E[c] : 0.0f, lo, hi, vin);
       }
-      warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb, (uint32_t)c, 0);
+      if (valid && !stiff) taylor_cell(a, (int)c, lo, hi, lam, lmax);
     }
   }
   // leave: tensor memory is freed by the warp that allocated it once every
@@ -740,7 +760,8 @@ int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N, int64_t
     b.job[0] = J;
     b.pol = a.pol;
     b.ws = a.ws;
-    e = launch_fb_f32(b, s->num_sms, st);
+    e = launch_stiff_f32(b, s->num_sms, st);
+    if (e == cudaSuccess) e = launch_fb_f32(b, s->num_sms, st);
   }
   if (e != cudaSuccess)
     return set_error(ION_ECUDA, "ion_step_surrogate launch: %s", cudaGetErrorString(e));
