@@ -106,9 +106,14 @@ def _ptr(a, t):
     return a.ctypes.data_as(t)
 
 
-def _consts(constants):
-    return np.ascontiguousarray(constants if constants is not None
-                                else PAPER_CONSTANTS, dtype=np.float64)
+#: rate models: Eq. 1 as printed (cycle-averaged), or the static-field rate
+ADK_CYCLE_AVERAGED = 0
+ADK_STATIC = 1
+
+
+def _consts(constants, model: int = ADK_CYCLE_AVERAGED):
+    c = list(constants if constants is not None else PAPER_CONSTANTS)[:3]
+    return np.ascontiguousarray(c + [float(model)], dtype=np.float64)
 
 
 def flm(l: int, m: int, _lib=None) -> float:
@@ -116,9 +121,10 @@ def flm(l: int, m: int, _lib=None) -> float:
 
 
 def adk_rate(E: float, U: float, l: int, m: int, Q: int, constants=None,
-             _lib=None) -> float:
-    """Eq. 1, W in 1/fs, for one transition with charge after ionization Q."""
-    c = _consts(constants)
+             _lib=None, model: int = ADK_CYCLE_AVERAGED) -> float:
+    """Eq. 1, W in 1/fs, for one transition with charge after ionization Q
+    (model ADK_STATIC: without the cycle-averaging factor)."""
+    c = _consts(constants, model)
     return (_lib or lib()).or_adk_rate(float(E), float(U), int(l), int(m),
                                        int(Q), _ptr(c, _dp))
 
@@ -135,12 +141,12 @@ class Species:
     """Per-state data of one gas: U_k (eV), l_k, m_k for k = 0..Z-1, where
     state k is ionized to k+1 by the rate W_k."""
 
-    def __init__(self, U, l, m, constants=None):
+    def __init__(self, U, l, m, constants=None, model: int = ADK_CYCLE_AVERAGED):
         self.U = np.ascontiguousarray(U, dtype=np.float64)
         self.l = np.ascontiguousarray(l, dtype=np.int32)
         self.m = np.ascontiguousarray(m, dtype=np.int32)
         self.Z = int(self.U.shape[0])
-        self.constants = _consts(constants)
+        self.constants = _consts(constants, model)
 
     def _args(self):
         return (self.Z, _ptr(self.U, _dp), _ptr(self.l, _ip), _ptr(self.m, _ip),

@@ -70,13 +70,17 @@ double or_flm(int l, int m) {
 /*   U_eV   : ionization potential of the state being ionized, eV            */
 /*   l, m   : orbital quantum number and its projection                      */
 /*   Q      : charge number after ionization                                 */
-/*   consts : {omega_a [1/s], E_a [GV/m], U_H [eV]}                          */
+/*   consts : {omega_a [1/s], E_a [GV/m], U_H [eV], model}                   */
+/*            model 0: Eq. 1 as printed (cycle-averaged);                    */
+/*            model 1: the static-field rate, Eq. 1 without the factor       */
+/*            sqrt(3 n*^3 E / (pi Q^3 E_a)) that averages over a cycle.      */
 /* ------------------------------------------------------------------------- */
 double or_adk_rate(double E_GVm, double U_eV, int l, int m, int Q,
                    const double *consts) {
   const double omega_a = consts[0];
   const double E_a = consts[1];
   const double U_H = consts[2];
+  const int model = (int)consts[3];
   const double E = fabs(E_GVm);
   const int am = m < 0 ? -m : m;
   const double q = (double)Q;
@@ -85,8 +89,10 @@ double or_adk_rate(double E_GVm, double U_eV, int l, int m, int Q,
   const double expo = (2.0 * E_a / (3.0 * E)) * pow(q / nstar, 3.0);
   if (expo > 700.0) return 0.0;
   const double e = exp(1.0);
+  const double cycle =
+      model == 1 ? 1.0 : sqrt(3.0 * pow(nstar, 3.0) * E / (M_PI * pow(q, 3.0) * E_a));
   const double W =
-      omega_a * sqrt(3.0 * pow(nstar, 3.0) * E / (M_PI * pow(q, 3.0) * E_a)) *
+      omega_a * cycle *
       (q * q) / (2.0 * nstar * nstar) * pow(2.0 * e / nstar, 2.0 * nstar) *
       exp(-expo) *
       ((2.0 * l + 1.0) * or_factorial(l + am)) /

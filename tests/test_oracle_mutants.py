@@ -11,8 +11,10 @@ MUTANTS = {
     "drop_m_in_power": [("2.0 * nstar - (double)am - 1.0);", "2.0 * nstar - 1.0);")],
     # Eq. 1: the cycle-averaging square root lost
     "drop_sqrt_factor": [(
-        "omega_a * sqrt(3.0 * pow(nstar, 3.0) * E / (M_PI * pow(q, 3.0) * E_a)) *",
-        "omega_a * 1.0 *")],
+        "model == 1 ? 1.0 : sqrt(3.0 * pow(nstar, 3.0) * E / (M_PI * pow(q, 3.0) * E_a));",
+        "1.0;")],
+    # static-field model: the cycle-averaging factor kept
+    "static_keeps_sqrt": [("model == 1 ? 1.0 :", "model == 2 ? 1.0 :")],
     # Eq. 1: sign of the tunnelling exponent
     "exponent_sign": [("      exp(-expo) *", "      exp(expo) *")],
     # Eq. 1: Q taken as the charge before ionization
@@ -39,6 +41,7 @@ PIN_TESTS = [
     (P.test_adk_hydrogenic_ion_closed_form, (1500.0,)),
     (P.test_adk_m_projection_ratio, (2, 300.0)),
     (P.test_adk_log_slope, (1, 800.0)),
+    (P.test_adk_static_hydrogen_landau_lifshitz, (300.0,)),
     (P.test_expm_vs_arbitrary_precision, ([13.7, 49.7, 191.9, 142.6, 290.4],)),
     (P.test_expm_vs_arbitrary_precision, ([2500.0, 0.2, 1e-30, 7.0],)),
     (P.test_paper_four_level_solution, ((0.9, 2.7, 0.05),)),

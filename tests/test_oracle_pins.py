@@ -82,6 +82,37 @@ def test_adk_log_slope(k, E):
     assert got == pytest.approx(want, rel=1e-6, abs=1e-6)
 
 
+@pytest.mark.parametrize("E", [300.0, 1000.0, 4000.0])
+def test_adk_static_hydrogen_landau_lifshitz(E):
+    # Static-field model (Eq. 1 without its cycle-averaging factor), Q = 1,
+    # U = U_H, l = m = 0: by hand W = w_a (2e^2/pi)(E_a/E) exp(-2E_a/(3E)).
+    # The textbook static-field rate of the hydrogen ground state (Landau &
+    # Lifshitz, Quantum Mechanics, Sec. 77) is 4 w_a (E_a/E) exp(-2E_a/(3E))
+    # in atomic units.  Eq. 1's coefficient (2e/n*)^(2n*)/(2 pi n*) ... gives
+    # 2e^2/pi in place of the exact 4, so the two differ by e^2/(2 pi).
+    ll = 4 * OMEGA_A * (E_A / E) * math.exp(-2 * E_A / (3 * E)) * 1e-15
+    got = oracle.adk_rate(E, U_H, 0, 0, 1, model=oracle.ADK_STATIC)
+    assert got / ll == pytest.approx(math.e ** 2 / (2 * math.pi), rel=1e-13)
+
+
+@pytest.mark.parametrize("k", [0, 3, 6])
+@pytest.mark.parametrize("E", [800.0, 3000.0])
+def test_adk_static_log_slope(k, E):
+    # Without the factor sqrt(3 n*^3 E/(pi Q^3 E_a)) the slope loses 1/2:
+    # d ln W / d ln E = -(2n* - |m| - 1) + (2/3)(Q/n*)^3 E_a/E.
+    Q = k + 1
+    ns = Q * math.sqrt(U_H / N2_U[k])
+    want = -(2 * ns - 1.0) + (2.0 / 3.0) * (Q / ns) ** 3 * E_A / E
+    h = 1e-5
+    st = oracle.ADK_STATIC
+    w1 = oracle.adk_rate(E * math.exp(h), N2_U[k], N2_L[k], 0, Q, model=st)
+    w0 = oracle.adk_rate(E * math.exp(-h), N2_U[k], N2_L[k], 0, Q, model=st)
+    if w1 <= 0 or w0 <= 0:
+        pytest.skip("rate underflows at this field")
+    got = (math.log(w1) - math.log(w0)) / (2 * h)
+    assert got == pytest.approx(want, rel=1e-6, abs=1e-6)
+
+
 def test_adk_cutoffs_and_units():
     # Zero field and fields whose exponent exceeds 700 give W = 0.
     assert oracle.adk_rate(0.0, 14.53, 1, 0, 1) == 0.0
