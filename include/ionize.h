@@ -66,13 +66,23 @@ extern "C" {
 
 typedef struct ion_species ion_species; /* opaque, owned by the library */
 
-/* Constants of Eq. 1.  NULL selects the printed values omega_a = 4.13e16 1/s
- * and E_a = 510 GV/m (Sec. 2, text after Eq. 1) with U_H = 13.6 eV (U_H is
- * named there but not given a value). */
+/* Rate models of ion_constants.rate_model. */
+#define ION_ADK_CYCLE_AVERAGED 0 /* Eq. 1 as printed */
+#define ION_ADK_STATIC 1         /* Eq. 1 without its cycle-averaging factor */
+                                 /* sqrt(3 n*^3 |E| / (pi Q^3 E_a)): the rate */
+                                 /* in a static field of magnitude |E|, for   */
+                                 /* fields given as instantaneous values      */
+
+/* Constants of Eq. 1 and the rate model.  NULL selects the printed values
+ * omega_a = 4.13e16 1/s and E_a = 510 GV/m (Sec. 2, text after Eq. 1) with
+ * U_H = 13.6 eV (U_H is named there but not given a value) and
+ * ION_ADK_CYCLE_AVERAGED.  CODATA values (omega_a = 4.1341374e16 1/s,
+ * E_a = 514.22067 GV/m, U_H = 13.605693 eV) are one choice of the others. */
 typedef struct {
   double omega_a_per_s;
   double E_a_GVm;
   double U_H_eV;
+  int rate_model; /* ION_ADK_CYCLE_AVERAGED or ION_ADK_STATIC */
 } ion_constants;
 
 /* Per-call policy of ion_step.  NULL selects the defaults. */

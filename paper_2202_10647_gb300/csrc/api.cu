@@ -62,12 +62,16 @@ void build_table(const double* U, const int* l, const int* m, int Z,
     const double Q = (double)(k + 1);
     const int am = m[k] < 0 ? -m[k] : m[k];
     const double ns = Q * std::sqrt(c.U_H_eV / U[k]);
-    const double b = 2.0 * ns - (double)am - 1.5;
+    // the cycle-averaging factor sqrt(3 n*^3 |E| / (pi Q^3 E_a)) contributes
+    // |E|^(1/2), i.e. -1/2 to the power of E_a/|E|
+    const bool avg = c.rate_model != ION_ADK_STATIC;
+    const double b = 2.0 * ns - (double)am - (avg ? 1.5 : 1.0);
     const double cnat = (2.0 / 3.0) * std::pow(Q / ns, 3.0);
     const double flm = (2.0 * l[k] + 1.0) * factorial(l[k] + am) /
                        (std::ldexp(1.0, am) * factorial(am) * factorial(l[k] - am));
     const double log2A =
-        std::log2(omega_fs) + 0.5 * std::log2(3.0 * ns * ns * ns / (M_PI * Q * Q * Q)) +
+        std::log2(omega_fs) +
+        (avg ? 0.5 * std::log2(3.0 * ns * ns * ns / (M_PI * Q * Q * Q)) : 0.0) +
         std::log2(Q * Q / (2.0 * ns * ns)) + 2.0 * ns * std::log2(2.0 * M_E / ns) +
         std::log2(flm / (2.0 * M_PI * ns)) +
         (2.0 * ns - (double)am - 1.0) * std::log2(2.0 * Q * Q * Q / (ns * ns * ns));
@@ -140,10 +144,14 @@ int ion_species_init(const double* U_ion_eV, const int* l, const int* m, int Z,
     if (l[k] < 0 || l[k] > 20 || am > l[k])
       return fail(ION_EINVAL, "state %d: need 0 <= |m| <= l <= 20 (l=%d m=%d)", k, l[k], m[k]);
   }
-  ion_constants cc = {4.13e16, 510.0, 13.6};
+  ion_constants cc = {4.13e16, 510.0, 13.6, ION_ADK_CYCLE_AVERAGED};
   if (c) {
-    if (!(c->omega_a_per_s > 0) || !(c->E_a_GVm > 0) || !(c->U_H_eV > 0))
-      return fail(ION_EINVAL, "constants must be > 0");
+    if (!(c->omega_a_per_s > 0) || !(c->E_a_GVm > 0) || !(c->U_H_eV > 0) ||
+        !std::isfinite(c->omega_a_per_s) || !std::isfinite(c->E_a_GVm) ||
+        !std::isfinite(c->U_H_eV))
+      return fail(ION_EINVAL, "constants must be finite and > 0");
+    if (c->rate_model != ION_ADK_CYCLE_AVERAGED && c->rate_model != ION_ADK_STATIC)
+      return fail(ION_EINVAL, "unknown rate_model %d", c->rate_model);
     cc = *c;
   }
   ion_species* sp = new (std::nothrow) ion_species();

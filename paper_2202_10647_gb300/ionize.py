@@ -65,7 +65,15 @@ class IonError(RuntimeError):
 
 class _Constants(ctypes.Structure):
     _fields_ = [("omega_a_per_s", ctypes.c_double), ("E_a_GVm", ctypes.c_double),
-                ("U_H_eV", ctypes.c_double)]
+                ("U_H_eV", ctypes.c_double), ("rate_model", ctypes.c_int)]
+
+
+#: rate models (ion_constants.rate_model)
+ION_ADK_CYCLE_AVERAGED = 0
+ION_ADK_STATIC = 1
+#: the printed constants of Eq. 1 with U_H = 13.6 eV, and CODATA values
+PAPER_CONSTANTS = (4.13e16, 510.0, 13.6)
+CODATA_CONSTANTS = (4.1341374e16, 514.22067, 13.605693)
 
 
 class _StepOpts(ctypes.Structure):
@@ -211,7 +219,7 @@ class Species:
     """ADK table of one gas (ion_species_init).  U, l, m are sequences of
     length Z for the Z ionizing transitions k -> k+1."""
 
-    def __init__(self, U, l, m, constants=None):
+    def __init__(self, U, l, m, constants=None, rate_model: int = ION_ADK_CYCLE_AVERAGED):
         U = [float(x) for x in U]
         l = [int(x) for x in l]
         m = [int(x) for x in m]
@@ -224,8 +232,10 @@ class Species:
         la = (ctypes.c_int * Z)(*l)
         ma = (ctypes.c_int * Z)(*m)
         c = None
-        if constants is not None:
-            c = ctypes.byref(_Constants(*[float(x) for x in constants]))
+        if constants is not None or rate_model != ION_ADK_CYCLE_AVERAGED:
+            cs = PAPER_CONSTANTS if constants is None else constants
+            c = ctypes.byref(_Constants(*[float(x) for x in cs][:3], int(rate_model)))
+        self.rate_model = int(rate_model)
         h = _vp()
         _check(lib().ion_species_init(Ua, la, ma, Z, c, ctypes.byref(h)))
         self._h = h

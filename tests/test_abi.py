@@ -50,6 +50,14 @@ def test_host_side_rejections():
     neg = (ctypes.c_double * 3)(10.0, -1.0, 30.0)
     assert lib.ion_species_init(neg, i3, i3, 3, None, ctypes.byref(h)) == ionize.ION_EINVAL
     assert lib.ion_species_init(d, i3, i3, 3, None, None) == ionize.ION_EINVAL
+    # an unknown rate model and bad constants are rejected before any CUDA call
+    bad_model = ionize._Constants(4.13e16, 510.0, 13.6, 7)
+    assert lib.ion_species_init(d, i3, i3, 3, ctypes.byref(bad_model),
+                                ctypes.byref(h)) == ionize.ION_EINVAL
+    assert b"rate_model" in lib.ion_last_error()
+    bad_const = ionize._Constants(4.13e16, -510.0, 13.6, ionize.ION_ADK_STATIC)
+    assert lib.ion_species_init(d, i3, i3, 3, ctypes.byref(bad_const),
+                                ctypes.byref(h)) == ionize.ION_EINVAL
     # NULL species is rejected before anything else
     assert lib.ion_step(None, None, None, 0, 0, 0.05, None, None, None, None, None, 0,
                         None, 0, None) == ionize.ION_EINVAL
