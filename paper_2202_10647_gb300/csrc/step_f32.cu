@@ -114,6 +114,7 @@ __device__ __forceinline__ bool bytes_equal(uint32_t x) {
 
 // Job of a chunk (jobs are few; chunks are numbered job after job).
 __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
+  if (a.njobs == 1) return 0;  // uniform: the single-species call
   int j = 0;
 #pragma unroll
   for (int i = 1; i < kMaxJobs; ++i)
@@ -199,11 +200,21 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
 #pragma unroll
-      for (int i = WM - 1; i >= 0; --i) {
+      for (int i = WM - 2; i >= 0; --i) {
         u[j][i] = fmaf(-lam[j][i], u[j][i], i > 0 ? lam[j][i - 1] * u[j][i - 1] : 0.0f);
         inc[j][i] = fmaf(u[j][i], ck, inc[j][i]);
       }
     }
+  }
+  // the last slot by conservation: the top state of a window of width WM
+  // gains what the others lost (narrower windows reach their top inside the
+  // series, whose rate there is zero, and never read this slot)
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    float t = 0.0f;
+#pragma unroll
+    for (int i = 0; i < WM - 1; ++i) t -= inc[j][i];
+    inc[j][WM - 1] = t;
   }
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
