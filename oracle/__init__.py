@@ -88,7 +88,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.or_step.restype = ctypes.c_int
     lib.or_step.argtypes = [ctypes.c_int, _dp, _ip, _ip, _dp, ctypes.c_int64,
                             _dp, _dp, ctypes.c_int64, ctypes.c_double, _u8p, _u8p,
-                            _dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+                            _dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int]
     lib.or_num_threads.restype = ctypes.c_int
     lib.or_num_threads.argtypes = []
     return lib
@@ -166,11 +167,20 @@ def rates(sp: Species, E, k_lo: int, k_hi: int, nthreads: int = 0,
     return W
 
 
+#: window policies: the paper's shift rule, and the adaptive width
+WINDOW_FIXED = 0
+WINDOW_ADAPTIVE = 1
+
+
 def step(sp: Species, E, N, dt: float, lo, hi, n_gas=None,
          eps_shift: float = 1e-6, window_update: bool = True,
-         nthreads: int = 0, _lib=None):
+         nthreads: int = 0, _lib=None, policy: int = WINDOW_FIXED,
+         w_min: int = 2, w_max: int = 6, eps_grow: float = 1e-6):
     """One windowed analytic step.  Returns (N', lo', hi', dne) as new arrays;
-    N has shape (Z+1, ncells)."""
+    N has shape (Z+1, ncells).  policy WINDOW_ADAPTIVE: after the step, while
+    the lowest state holds less than eps_shift it is dropped (width above
+    w_min) or the window slides; then, if the old top state holds more than
+    eps_grow, the state above joins (width at most w_max)."""
     E = np.ascontiguousarray(E, dtype=np.float64)
     N = np.array(N, dtype=np.float64, order="C", copy=True)
     lo = np.array(lo, dtype=np.uint8, copy=True)
@@ -185,6 +195,7 @@ def step(sp: Species, E, N, dt: float, lo, hi, n_gas=None,
                                  _ptr(dne, _dp),
                                  None if ng is None else _ptr(ng, _dp),
                                  float(eps_shift), int(bool(window_update)),
+                                 int(policy), int(w_min), int(w_max), float(eps_grow),
                                  int(nthreads))
     if rc != 0:
         raise ValueError(f"or_step rejected its arguments ({rc})")

@@ -194,12 +194,18 @@ int or_rates(int Z, const double *U, const int *l, const int *m,
 /*   lo, hi : window bounds per cell; in/out                                 */
 /*   dne    : out, newly freed electrons per cell (x n_gas if non-null)      */
 /*   window_update : 0 keeps the windows fixed                               */
+/*   policy : 0 the paper's rule (Sec. 3): slide up while the lowest state   */
+/*            holds less than eps_shift, width kept;                         */
+/*            1 adaptive: while the lowest state holds less than eps_shift,  */
+/*            drop it if the width exceeds wmin, else slide; then, if the    */
+/*            old top state holds more than eps_grow, add the state above    */
+/*            (width at most wmax).                                          */
 /* ------------------------------------------------------------------------- */
 int or_step(int Z, const double *U, const int *l, const int *m,
             const double *consts, int64_t ncells, const double *E, double *N,
             int64_t ld, double dt, uint8_t *lo, uint8_t *hi, double *dne,
             const double *n_gas, double eps_shift, int window_update,
-            int nthreads) {
+            int policy, int wmin, int wmax, double eps_grow, int nthreads) {
   if (Z < 1 || Z >= OR_MAXW || ld < ncells || dt < 0.0) return -1;
   for (int64_t c = 0; c < ncells; ++c)
     if (lo[c] > hi[c] || hi[c] > Z) return -2;
@@ -230,13 +236,29 @@ int or_step(int Z, const double *U, const int *l, const int *m,
     for (int i = 0; i < w; ++i) d += (double)(a + i) * (n1[i] - n0[i]);
     dne[c] = n_gas ? d * n_gas[c] : d;
     for (int i = 0; i < w; ++i) N[(int64_t)(a + i) * ld + c] = n1[i];
-    if (window_update) {
+    if (window_update && policy == 0) {
       int na = a, nb = b, shifts = 0;
       while (shifts < w - 1 && nb < Z && N[(int64_t)na * ld + c] < eps_shift) {
         ++na;
         ++nb;
         ++shifts;
       }
+      lo[c] = (uint8_t)na;
+      hi[c] = (uint8_t)nb;
+    } else if (window_update) {
+      int na = a, nb = b;
+      for (int moves = 0; moves < w - 1; ++moves) {
+        if (!(N[(int64_t)na * ld + c] < eps_shift)) break;
+        if (nb - na + 1 > wmin) {
+          ++na;
+        } else if (nb < Z) {
+          ++na;
+          ++nb;
+        } else {
+          break;
+        }
+      }
+      if (N[(int64_t)b * ld + c] > eps_grow && nb < Z && nb - na + 1 < wmax) ++nb;
       lo[c] = (uint8_t)na;
       hi[c] = (uint8_t)nb;
     }

@@ -34,6 +34,10 @@ MUTANTS = {
                         "d += (double)(a + i) * n1[i];")],
     # window update: slides past the top state
     "slide_past_top": [("shifts < w - 1 && nb < Z &&", "shifts < w - 1 && nb <= Z &&")],
+    # adaptive window: grows one state past w_max
+    "grow_past_wmax": [("nb < Z && nb - na + 1 < wmax) ++nb;", "nb < Z && nb - na + 1 <= wmax) ++nb;")],
+    # adaptive window: drops the bottom below w_min instead of sliding
+    "shrink_below_wmin": [("if (nb - na + 1 > wmin) {", "if (nb - na + 1 >= wmin) {")],
 }
 
 PIN_TESTS = [
@@ -48,6 +52,7 @@ PIN_TESTS = [
     (P.test_step_four_level_matches_paper, ()),
     (P.test_step_single_level_closed_form, ()),
     (P.test_window_update_rules, ()),
+    (P.test_adaptive_window_rules, ()),
 ]
 
 

@@ -366,6 +366,42 @@ def test_window_update_rules():
     assert np.array_equal(lo2, lo) and np.array_equal(hi2, hi)
 
 
+def test_adaptive_window_rules():
+    """The adaptive policy on hand-made cells at zero field (populations
+    unchanged), each expected window worked out by hand from the rule."""
+    sp = nitrogen()
+    N = np.zeros((8, 5))
+    N[1:3, 0] = 0.5            # [0,3]: empty bottom dropped -> [1,3]
+    N[3, 1] = 1.0              # [2,3] at w_min: slides, full top grows -> [3,5]
+    N[7, 2] = 1.0              # [4,7]: shrinks to w_min at the top -> [6,7]
+    N[1:6, 3] = 0.18           # [1,6] at w_max with a populated top -> [1,6]
+    N[6, 3] = 0.1
+    N[0, 4] = 0.6              # [0,2], populated top -> grows to [0,3]
+    N[2, 4] = 0.4
+    lo = np.array([0, 2, 4, 1, 0], np.uint8)
+    hi = np.array([3, 3, 7, 6, 2], np.uint8)
+    E = np.zeros(5)
+    N1, lo1, hi1, dne = oracle.step(sp, E, N, 0.05, lo, hi, policy=oracle.WINDOW_ADAPTIVE,
+                                    w_min=2, w_max=6, eps_grow=1e-6)
+    assert np.array_equal(N1, N) and np.all(dne == 0)
+    assert list(zip(lo1, hi1)) == [(1, 3), (3, 5), (6, 7), (1, 6), (0, 3)]
+    # w_min = 3: the bottom is dropped once, then the window slides
+    M = np.zeros((8, 1))
+    M[2:4, 0] = 0.5
+    _, lo2, hi2, _ = oracle.step(sp, np.zeros(1), M, 0.05, [0], [3],
+                                 policy=oracle.WINDOW_ADAPTIVE, w_min=3, w_max=6)
+    assert (lo2[0], hi2[0]) == (2, 5)
+    # with w_min = w_max = w and no growth it is the paper's rule
+    E2 = np.array([3000.0, 0.0])
+    P = np.zeros((8, 2))
+    P[0] = [1.0, 0.0]
+    P[1] = [0.0, 1.0]
+    a = oracle.step(sp, E2, P, 0.2, [0, 1], [3, 4])
+    b = oracle.step(sp, E2, P, 0.2, [0, 1], [3, 4], policy=oracle.WINDOW_ADAPTIVE,
+                    w_min=4, w_max=4, eps_grow=np.inf)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
 def test_window_width_one_and_dt_zero():
     sp = nitrogen()
     N = np.zeros((8, 2))
