@@ -85,6 +85,10 @@ typedef struct {
   int rate_model; /* ION_ADK_CYCLE_AVERAGED or ION_ADK_STATIC */
 } ion_constants;
 
+/* Window policies of ion_step_opts.window_policy. */
+#define ION_WINDOW_FIXED 0    /* the paper's rule: slide, width kept        */
+#define ION_WINDOW_ADAPTIVE 1 /* width adapts between w_min and w_max       */
+
 /* Per-call policy of ion_step.  NULL selects the defaults. */
 typedef struct {
   /* The window [lo,hi] slides up by one state while the population of its
@@ -97,6 +101,18 @@ typedef struct {
    * |W_i - W_j| < degen_gap * max(W_i, W_j) gets its Bateman coefficients in
    * FP64; default 1e-3.  0 disables the test. */
   double degen_gap;
+  /* ION_WINDOW_FIXED (default): the window slides as above.
+   * ION_WINDOW_ADAPTIVE: while the lowest state holds less than eps_shift
+   * (at most w-1 moves) it is dropped if the width exceeds w_min, else the
+   * window slides; then, if the old top state holds more than eps_grow, the
+   * state above joins (width at most w_max, never past Z).  Requires
+   * 2 <= w_min <= w_max <= ION_MAX_WINDOW and eps_grow >= 0; the paper has
+   * only the fixed rule (Sec. 3), this one trades window traffic for the
+   * lag of a fixed window behind fast ionization. */
+  int window_policy;
+  int w_min;
+  int w_max;
+  double eps_grow;
 } ion_step_opts;
 
 /* ion_species_init -- build the per-state ADK table of one gas (Eq. 1).

@@ -245,8 +245,16 @@ int check_flags(int flags) {
 int make_policy(double dt_fs, const ion_step_opts* opts, int flags, ion::Policy* pol) {
   if (!(dt_fs >= 0.0) || !std::isfinite(dt_fs))
     return fail(ION_EINVAL, "dt_fs must be finite and >= 0 (got %g)", dt_fs);
-  ion_step_opts o = {1e-6, 1e-3};
+  ion_step_opts o = {1e-6, 1e-3, ION_WINDOW_FIXED, 2, ION_MAX_WINDOW, 1e-6};
   if (opts) o = *opts;
+  if (o.window_policy != ION_WINDOW_FIXED && o.window_policy != ION_WINDOW_ADAPTIVE)
+    return fail(ION_EINVAL, "unknown window_policy %d", o.window_policy);
+  if (o.window_policy == ION_WINDOW_ADAPTIVE &&
+      (o.w_min < 2 || o.w_min > o.w_max || o.w_max > ION_MAX_WINDOW ||
+       !(o.eps_grow >= 0.0) || !std::isfinite(o.eps_grow)))
+    return fail(ION_EINVAL,
+                "adaptive windows need 2 <= w_min <= w_max <= %d and finite eps_grow >= 0",
+                ION_MAX_WINDOW);
   if (!(o.eps_shift >= 0.0) || !std::isfinite(o.eps_shift))
     return fail(ION_EINVAL, "eps_shift must be finite and >= 0");
   if (!(o.degen_gap >= 0.0) || !(o.degen_gap < 1.0))
@@ -256,6 +264,10 @@ int make_policy(double dt_fs, const ion_step_opts* opts, int flags, ion::Policy*
   pol->eps = o.eps_shift;
   pol->gap = o.degen_gap;
   pol->flags = flags;
+  pol->adaptive = o.window_policy == ION_WINDOW_ADAPTIVE;
+  pol->wmin = o.w_min;
+  pol->wmax = o.w_max;
+  pol->eps_grow = o.eps_grow;
   return ION_OK;
 }
 

@@ -104,6 +104,18 @@ __device__ __forceinline__ void append_record(const Scratch& S, bool take, int j
   }
 }
 
+// The window rule after a step (unless ION_NO_WINDOW_UPDATE): the paper's
+// slide, or the adaptive width.  v holds the window after the step.
+template <typename T, int WM>
+__device__ __forceinline__ void window_after_step(const JobIO& J, const Policy& pol,
+                                                  const T (&v)[WM], int w, int& lo, int& hi) {
+  if (pol.flags & ION_NO_WINDOW_UPDATE) return;
+  if (pol.adaptive)
+    adapt_window<T, WM>(v, w, J.Z, (T)pol.eps, pol.wmin, pol.wmax, (T)pol.eps_grow, lo, hi);
+  else if (v[0] < (T)pol.eps && hi < J.Z)
+    slide_window<T, WM>(v, w, J.Z, (T)pol.eps, lo, hi);
+}
+
 // ---------------------------------------------------------------------------
 // Update of one cell whose window populations v[0..w-1] and rates
 // lam[r] = W_{lo+r} dt (r < w-1; 0 beyond) are known (2 <= w <= WM): Taylor
@@ -132,8 +144,7 @@ __device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, i
           return true;
         dne = dd_update<T, WM>(v, lam, w);
       }
-      if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0)
-        slide_window<T, WM>(v, w, J.Z, (T)pol.eps, nlo, nhi);
+      window_after_step<T, WM>(J, pol, v, w, nlo, nhi);
       T* p = N + (int64_t)lo * J.ld + c;
 #pragma unroll
       for (int r = 0; r < WM; ++r) {
@@ -144,7 +155,7 @@ __device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, i
   }
   const T* __restrict__ G = static_cast<const T*>(J.n_gas);
   __stcs(static_cast<T*>(J.dne) + c, G ? dne * G[c] : dne);
-  if (nlo != lo) {
+  if (nlo != lo || nhi != hi) {
     J.lo[c] = (uint8_t)nlo;
     J.hi[c] = (uint8_t)nhi;
   }

@@ -466,4 +466,50 @@ __device__ __forceinline__ void slide_window(const T (&v)[WM], int w, int Z,
   }
 }
 
+// Adaptive window (ION_WINDOW_ADAPTIVE), after the step: while the lowest
+// state holds less than eps (at most w-1 moves) it is dropped if the width
+// exceeds wmin, else the window slides (never past hi = Z); then, if the old
+// top state holds more than eps_grow, the state above joins (width at most
+// wmax, never past Z).  v is the window after the step, w its width.
+// Kept out of line (scalar arguments, result lo | hi << 8) so that kernels
+// running the fixed rule carry none of it.
+template <typename T>
+__device__ __noinline__ int adapt_window_call(T v0, T v1, T v2, T v3, T v4, T v5, int w, int Z,
+                                              T eps, int wmin, int wmax, T eps_grow, int lo,
+                                              int hi) {
+  const T v[6] = {v0, v1, v2, v3, v4, v5};
+  bool go = true;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    go = go && (r < w - 1) && (v[r] < eps);
+    if (go) {
+      if (hi - lo + 1 > wmin) {
+        ++lo;
+      } else if (hi < Z) {
+        ++lo;
+        ++hi;
+      } else {
+        go = false;
+      }
+    }
+  }
+  T top = T(0);
+#pragma unroll
+  for (int r = 0; r < 6; ++r) top = (r == w - 1) ? v[r] : top;
+  if (top > eps_grow && hi < Z && hi - lo + 1 < wmax) ++hi;
+  return lo | (hi << 8);
+}
+
+template <typename T, int WM>
+__device__ __forceinline__ void adapt_window(const T (&v)[WM], int w, int Z, T eps, int wmin,
+                                             int wmax, T eps_grow, int& lo, int& hi) {
+  T u[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) u[r] = r < WM ? v[r < WM ? r : 0] : T(0);
+  const int p = adapt_window_call<T>(u[0], u[1], u[2], u[3], u[4], u[5], w, Z, eps, wmin, wmax,
+                                     eps_grow, lo, hi);
+  lo = p & 0xff;
+  hi = p >> 8;
+}
+
 }  // namespace ion

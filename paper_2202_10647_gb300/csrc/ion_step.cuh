@@ -45,6 +45,9 @@ struct Policy {
   double eps;
   double gap;
   int flags;
+  int adaptive;     // ION_WINDOW_ADAPTIVE
+  int wmin, wmax;   // adaptive widths
+  double eps_grow;  // adaptive: the top grows above this population
 };
 
 // Workspace views.

@@ -131,7 +131,7 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 // at most 4e-5 W dt; rates above kLamPrecise = 2^-6 (where that could reach
 // 6e-7) are recomputed in float-float.  The Taylor series runs the warp's
 // largest term count (extra terms only add accuracy).
-template <int Q, int WM>
+template <int Q, int WM, bool AD>
 __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
                                            const StagedF32& tab, const QStage<Q>& st,
                                            int lane, int c0, const float (&Ev)[Q],
@@ -232,8 +232,13 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     }
 #pragma unroll
     for (int r = 0; r < WM; ++r) v[j][r] += inc[j][r];
-    if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0 && v[j][0] < (float)pol.eps && hi[j] < J.Z)
-      slide_window<float, WM>(v[j], w[j], J.Z, (float)pol.eps, nlo[j], nhi[j]);
+    if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0) {
+      if constexpr (AD)
+        adapt_window<float, WM>(v[j], w[j], J.Z, (float)pol.eps, pol.wmin, pol.wmax,
+                                (float)pol.eps_grow, nlo[j], nhi[j]);
+      else if (v[j][0] < (float)pol.eps && hi[j] < J.Z)
+        slide_window<float, WM>(v[j], w[j], J.Z, (float)pol.eps, nlo[j], nhi[j]);
+    }
   }
   // stores
   const float* __restrict__ G = static_cast<const float*>(J.n_gas);
@@ -275,7 +280,7 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
   }
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
-    if (ok[j] && !stiff[j] && nlo[j] != lo[j]) {
+    if (ok[j] && !stiff[j] && (nlo[j] != lo[j] || nhi[j] != hi[j])) {
       J.lo[c0 + j] = (uint8_t)nlo[j];
       J.hi[c0 + j] = (uint8_t)nhi[j];
     }
@@ -292,7 +297,9 @@ constexpr size_t stream_smem(int njobs) {
   return (size_t)njobs * sizeof(StagedF32) + (size_t)W * kStages * sizeof(QStage<Q>);
 }
 
-template <int Q, int W>
+// AD: the adaptive window policy (a separate instantiation, so that the
+// fixed rule's kernels carry none of it).
+template <int Q, int W, bool AD>
 __global__ void __launch_bounds__(W * 32)
     ion_stream_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -446,11 +453,11 @@ __global__ void __launch_bounds__(W * 32)
       for (int j = 0; j < Q; ++j)
         if (ok[j]) __stcs(D + c0 + j, 0.0f);
     } else if (WMw == 2) {
-      easy_cells<Q, 2>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+      easy_cells<Q, 2, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
     } else if (WMw <= 4) {
-      easy_cells<Q, 4>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+      easy_cells<Q, 4, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
     } else {
-      easy_cells<Q, 6>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+      easy_cells<Q, 6, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
     }
     // stiff cells: their inputs (as loaded) go to the record queue
     bool any = false;
@@ -582,8 +589,7 @@ __device__ __forceinline__ void fb_cell(const JobIO& J, const Policy& pol,
     N[(int64_t)(lo + r) * J.ld + c] = vf[r];
   }
   int nlo = lo, nhi = hi;
-  if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0)
-    slide_window<float, W>(vf, W, J.Z, (float)pol.eps, nlo, nhi);
+  window_after_step<float, W>(J, pol, vf, W, nlo, nhi);
   const float* G = static_cast<const float*>(J.n_gas);
   const float d = __double2float_rn(dne);
   static_cast<float*>(J.dne)[c] = G ? d * G[c] : d;
@@ -634,6 +640,7 @@ size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 struct StreamVariant {
   const void* fn;
   int Q, W;
+  bool adaptive;
   size_t (*smem)(int);
 };
 
@@ -642,16 +649,19 @@ size_t smem_of(int njobs) {
   return stream_smem<Q, W>(njobs);
 }
 
-#define ION_VARIANT(Q, W) \
-  { reinterpret_cast<const void*>(&ion_stream_kernel<Q, W>), Q, W, &smem_of<Q, W> }
-const StreamVariant kVariants[] = {ION_VARIANT(1, 2), ION_VARIANT(1, 4), ION_VARIANT(1, 8),
-                                   ION_VARIANT(2, 2), ION_VARIANT(2, 4), ION_VARIANT(2, 8),
-                                   ION_VARIANT(4, 2), ION_VARIANT(4, 4), ION_VARIANT(4, 8)};
+#define ION_VARIANT(Q, W, AD) \
+  { reinterpret_cast<const void*>(&ion_stream_kernel<Q, W, AD>), Q, W, AD, &smem_of<Q, W> }
+#define ION_VARIANTS(AD)                                                          \
+  ION_VARIANT(1, 2, AD), ION_VARIANT(1, 4, AD), ION_VARIANT(1, 8, AD),             \
+      ION_VARIANT(2, 2, AD), ION_VARIANT(2, 4, AD), ION_VARIANT(2, 8, AD),         \
+      ION_VARIANT(4, 2, AD), ION_VARIANT(4, 4, AD), ION_VARIANT(4, 8, AD)
+const StreamVariant kVariants[] = {ION_VARIANTS(false), ION_VARIANTS(true)};
+#undef ION_VARIANTS
 #undef ION_VARIANT
 
-const StreamVariant* find_variant(int Q, int W) {
+const StreamVariant* find_variant(int Q, int W, bool adaptive = false) {
   for (const auto& v : kVariants)
-    if (v.Q == Q && v.W == W) return &v;
+    if (v.Q == Q && v.W == W && v.adaptive == adaptive) return &v;
   return nullptr;
 }
 
@@ -728,7 +738,8 @@ void bind_workspace(Scratch& s, void* ws, int64_t ncells) {
 
 cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms,
                              cudaStream_t s) {
-  const StreamVariant* v = find_variant(shape.cells_per_lane, shape.warps_per_block);
+  const StreamVariant* v =
+      find_variant(shape.cells_per_lane, shape.warps_per_block, a.pol.adaptive != 0);
   if (!v) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.ws.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;

@@ -207,8 +207,7 @@ __device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, in
       p += J.ld;
     }
     dne = taylor_propagate<float, ION_MAX_WINDOW>(v, lam, w, lmax);
-    if ((a.pol.flags & ION_NO_WINDOW_UPDATE) == 0)
-      slide_window<float, ION_MAX_WINDOW>(v, w, J.Z, (float)a.pol.eps, nlo, nhi);
+    window_after_step<float, ION_MAX_WINDOW>(J, a.pol, v, w, nlo, nhi);
     float* q = N + (int64_t)lo * J.ld + c;
 #pragma unroll
     for (int r = 0; r < ION_MAX_WINDOW; ++r) {
@@ -218,7 +217,7 @@ __device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, in
   }
   const float* __restrict__ G = static_cast<const float*>(J.n_gas);
   __stcs(static_cast<float*>(J.dne) + c, G ? dne * G[c] : dne);
-  if (nlo != lo) {
+  if (nlo != lo || nhi != hi) {
     J.lo[c] = (uint8_t)nlo;
     J.hi[c] = (uint8_t)nhi;
   }

@@ -77,7 +77,24 @@ CODATA_CONSTANTS = (4.1341374e16, 514.22067, 13.605693)
 
 
 class _StepOpts(ctypes.Structure):
-    _fields_ = [("eps_shift", ctypes.c_double), ("degen_gap", ctypes.c_double)]
+    _fields_ = [("eps_shift", ctypes.c_double), ("degen_gap", ctypes.c_double),
+                ("window_policy", ctypes.c_int), ("w_min", ctypes.c_int),
+                ("w_max", ctypes.c_int), ("eps_grow", ctypes.c_double)]
+
+
+#: window policies (ion_step_opts.window_policy)
+ION_WINDOW_FIXED = 0
+ION_WINDOW_ADAPTIVE = 1
+
+
+def _opts(eps_shift=1e-6, degen_gap=1e-3, window=None) -> _StepOpts:
+    """ion_step_opts; window = None (the paper's rule) or a dict with
+    w_min, w_max and eps_grow for the adaptive policy."""
+    if window is None:
+        return _StepOpts(float(eps_shift), float(degen_gap), ION_WINDOW_FIXED, 2, 6, 1e-6)
+    return _StepOpts(float(eps_shift), float(degen_gap), ION_WINDOW_ADAPTIVE,
+                     int(window.get("w_min", 2)), int(window.get("w_max", 6)),
+                     float(window.get("eps_grow", 1e-6)))
 
 
 class _BatchJob(ctypes.Structure):
@@ -288,9 +305,10 @@ def step(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
          k_hi: torch.Tensor, dt: float, dne: torch.Tensor,
          n_gas: torch.Tensor | None = None, ws: torch.Tensor | None = None,
          eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32,
-         ncells: int | None = None) -> torch.Tensor:
+         ncells: int | None = None, window: dict | None = None) -> torch.Tensor:
     """One ion_step.  N is (Z+1, ld) and is updated in place, as are k_lo and
-    k_hi; dne is written.  Returns the workspace (its header holds the
+    k_hi; dne is written.  window: None (the paper's slide) or
+    {"w_min": .., "w_max": .., "eps_grow": ..} for ION_WINDOW_ADAPTIVE.  Returns the workspace (its header holds the
     counters described in include/ionize.h)."""
     f64 = bool(flags & ION_F64_PLAIN)
     dt_ = torch.float64 if f64 else torch.float32
@@ -308,7 +326,7 @@ def step(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
     if ws is None:
         ws = workspace(n, flags, dev)
     _need(ws, "ws", torch.uint8, dev)
-    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    opts = _opts(eps_shift, degen_gap, window)
     _check(lib().ion_step(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
                           _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
                           ctypes.byref(opts), int(flags), _ptr(ws), ws.numel(),
@@ -320,7 +338,7 @@ def step_noalloc(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tens
                  k_hi: torch.Tensor, dt: float, dne: torch.Tensor,
                  n_gas: torch.Tensor | None = None, eps_shift: float = 1e-6,
                  degen_gap: float = 1e-3, flags: int = ION_F32,
-                 ncells: int | None = None) -> None:
+                 ncells: int | None = None, window: dict | None = None) -> None:
     """ion_step_noalloc: the same step as `step`, with the library's own
     fixed scratch array instead of a workspace (at most
     ION_STEP_NOALLOC_MAX_CELLS cells per call)."""
@@ -337,7 +355,7 @@ def step_noalloc(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tens
     if N.dim() != 2 or N.shape[0] != sp.Z + 1:
         raise ValueError(f"N must have shape (Z+1, ld) = ({sp.Z + 1}, ld)")
     n = E.numel() if ncells is None else int(ncells)
-    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    opts = _opts(eps_shift, degen_gap, window)
     _check(lib().ion_step_noalloc(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
                                   _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
                                   ctypes.byref(opts), int(flags), _stream(E)))
@@ -376,14 +394,15 @@ def batched_workspace(jobs, flags: int = ION_F32, device=None) -> torch.Tensor:
 
 def step_batched(jobs, dt: float, ws: torch.Tensor | None = None, eps_shift: float = 1e-6,
                  degen_gap: float = 1e-3, flags: int = ION_F32,
-                 shape: LaunchShape | tuple | None = None) -> torch.Tensor:
+                 shape: LaunchShape | tuple | None = None,
+                 window: dict | None = None) -> torch.Tensor:
     """ion_step_batched over jobs = [(Species, E, N, k_lo, k_hi, dne[, n_gas]), ...]."""
     arr, dev = _jobs(jobs, bool(flags & ION_F64_PLAIN))
     if ws is None:
         ws = batched_workspace(jobs, flags, dev)
     if shape is not None and not isinstance(shape, LaunchShape):
         shape = LaunchShape(*shape)
-    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    opts = _opts(eps_shift, degen_gap, window)
     _check(lib().ion_step_batched(arr, len(jobs), float(dt), ctypes.byref(opts), int(flags),
                                   ctypes.byref(shape) if shape is not None else None,
                                   _ptr(ws), ws.numel(), _stream(jobs[0][1])))
@@ -391,12 +410,13 @@ def step_batched(jobs, dt: float, ws: torch.Tensor | None = None, eps_shift: flo
 
 
 def autotune(jobs, dt: float, ws: torch.Tensor | None = None, reps: int = 3,
-             eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32):
+             eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32,
+             window: dict | None = None):
     """ion_autotune: (best LaunchShape, its median ms).  Steps the jobs' arrays."""
     arr, dev = _jobs(jobs)
     if ws is None:
         ws = batched_workspace(jobs, flags, dev)
-    opts = _StepOpts(float(eps_shift), float(degen_gap))
+    opts = _opts(eps_shift, degen_gap, window)
     best = LaunchShape()
     ms = ctypes.c_float()
     _check(lib().ion_autotune(arr, len(jobs), float(dt), ctypes.byref(opts), int(flags),
@@ -557,7 +577,7 @@ class Surrogate:
     def step(self, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor, k_hi: torch.Tensor,
              dt: float, dne: torch.Tensor, n_gas: torch.Tensor | None = None,
              ws: torch.Tensor | None = None, eps_shift: float = 1e-6, degen_gap: float = 1e-3,
-             pop_tol: float = 1e-6) -> torch.Tensor:
+             pop_tol: float = 1e-6, window: dict | None = None) -> torch.Tensor:
         """ion_step_surrogate; returns the workspace (header words 3, 4, 5:
         cells on the network's rates, on Eq. 1's rates, timeout flag)."""
         _need(E, "E", torch.float32)
@@ -572,7 +592,7 @@ class Surrogate:
             raise ValueError(f"N must have shape (Z+1, ld) = ({self.Z + 1}, ld)")
         n = E.numel()
         ws = workspace(n, ION_F32, dev) if ws is None else ws
-        opts = _StepOpts(float(eps_shift), float(degen_gap))
+        opts = _opts(eps_shift, degen_gap, window)
         _check(lib().ion_step_surrogate(self._h, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
                                         _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
                                         ctypes.byref(opts), float(pop_tol), _ptr(ws),

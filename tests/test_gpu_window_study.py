@@ -33,8 +33,10 @@ pytestmark = pytest.mark.gpu
 DT = 0.05
 
 
-def run_reduced(sd, fields, w, n, eps=1e-6):
-    """GPU FP64 form, window [0, w-1] at t = 0; populations after each step."""
+def run_reduced(sd, fields, w, n, eps=1e-6, window=None, widths=None):
+    """GPU FP64 form, window [0, w-1] at t = 0; populations after each step.
+    window: the adaptive policy's parameters (None: the paper's rule);
+    widths: a list that receives the mean window width after each step."""
     dev = "cuda"
     sp = gpu_species(sd)
     N = torch.zeros((sd.Z + 1, n), dtype=torch.float64, device=dev)
@@ -46,8 +48,10 @@ def run_reduced(sd, fields, w, n, eps=1e-6):
     out = []
     for E in fields:
         ionize.step(sp, E.to(dev), N, lo, hi, DT, dne, ws=ws, eps_shift=eps,
-                    flags=ionize.ION_F64_PLAIN)
+                    flags=ionize.ION_F64_PLAIN, window=window)
         out.append(N.cpu().numpy().copy())
+        if widths is not None:
+            widths.append(float((hi.double() - lo.double() + 1).mean()))
     return out
 
 
@@ -110,11 +114,23 @@ def test_window_width_study_nitrogen_and_krypton(capsys):
     for w in range(2, 7):
         res_k[w] = errors(run_reduced(sk, fk, w, E0.numel()), fullk, sk.Z)
         table.append(("Kr-like pulse", w) + res_k[w])
+    # the adaptive policy: width between w_min and w_max; traffic ~ mean width
+    ada = {}
+    for name, sd_, fl, fu, n_ in (("N 2D pulse", sd, fields, full, n),
+                                  ("Kr-like pulse", sk, fk, fullk, E0.numel())):
+        for win in (dict(w_min=2, w_max=6, eps_grow=1e-6), dict(w_min=3, w_max=5, eps_grow=1e-4)):
+            widths = []
+            red = run_reduced(sd_, fl, win["w_min"], n_, window=win, widths=widths)
+            tag = f"adaptive {win['w_min']}-{win['w_max']}"
+            ada[(name, tag)] = errors(red, fu, sd_.Z) + (float(np.mean(widths)),)
     with capsys.disabled():
         print("\nreduced window vs full system, maxima over cells: |N - N_full| at the "
               "end, |<k> - <k>_full| over all steps, at the end")
         for name, w, pop, charge_t, charge in table:
             print(f"  {name:14s} w={w}  {pop:.3e}  {charge_t:.3e}  {charge:.3e}")
+        print("adaptive policy (same columns, then the mean width over cells and steps)")
+        for (name, tag), (pop, charge_t, charge, mw) in ada.items():
+            print(f"  {name:14s} {tag}  {pop:.3e}  {charge_t:.3e}  {charge:.3e}  {mw:.2f}")
     # freed electrons at the end: the paper's four levels beat three, and a
     # wider window does not do worse (up to rounding)
     for res in (res_n, res_k):
