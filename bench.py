@@ -493,6 +493,9 @@ def main():
         graphs = {name: multistep.StepGraph(ksp, kfields, kwl.N, kwl.lo, kwl.hi, kdne, 0.05,
                                             ws=kws, conservation=chk)
                   for name, chk in (("with_check", True), ("steps_only", False))}
+        graphs["adaptive_window"] = multistep.StepGraph(
+            ksp, kfields, kwl.N, kwl.lo, kwl.hi, kdne, 0.05, ws=kws, conservation=False,
+            window=dict(w_min=2, w_max=6, eps_grow=1e-6))
         knet = None
         if not args.no_surrogate:
             from paper_2202_10647_gb300 import surrogate as S
@@ -507,7 +510,7 @@ def main():
             kwl.lo.zero_()
             kwl.hi.fill_(3)
 
-        kres = {}
+        kres, kwidth = {}, {}
         for name, g_ in graphs.items():
             ts_ = []
             for r_ in range(4):
@@ -521,6 +524,7 @@ def main():
                 if r_ >= 1:
                     ts_.append(a_.elapsed_time(b_))
             kres[name] = float(np.median(ts_))
+            kwidth[name] = float((kwl.hi.double() - kwl.lo.double() + 1).mean())
         cons = graphs["with_check"].cons.cpu().numpy()
         ksur = None
         if "surrogate_with_check" in graphs:
@@ -540,7 +544,13 @@ def main():
                                              "after_step_50": float(cons[-1]),
                                              "max": float(cons.max())},
                    "windows_slid_fraction": float((kwl.lo > 0).double().mean()),
-                   "surrogate_form": ksur}
+                   "surrogate_form": ksur,
+                   "adaptive_window_steps_only": {
+                       "policy": "w_min 2, w_max 6, eps_grow 1e-6",
+                       "ms_per_50_steps": kres["adaptive_window"],
+                       "value": 50 * kn / (kres["adaptive_window"] * 1e-3),
+                       "mean_width_after_50_steps": kwidth["adaptive_window"],
+                       "fixed_mean_width_after_50_steps": kwidth["steps_only"]}}
         del graphs, kfields, kwl, kws, kdne, knet
 
     # -- end to end through host buffers -------------------------------------

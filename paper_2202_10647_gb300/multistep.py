@@ -35,15 +35,16 @@ def _prime(sp: ionize.Species, flags: int, device) -> None:
 class StepGraph:
     """K = len(fields) steps: step s advances N, k_lo, k_hi by dt with the
     field fields[s] and writes dne (ion_step, or ion_step_surrogate when a
-    surrogate is given); with `conservation`, the largest |sum_k N_k - 1|
-    over the cells after step s lands in self.cons[s]."""
+    surrogate is given; `window` selects the adaptive window policy, as in
+    ionize.step); with `conservation`, the largest |sum_k N_k - 1| over the
+    cells after step s lands in self.cons[s]."""
 
     def __init__(self, sp: ionize.Species, fields, N: torch.Tensor, k_lo: torch.Tensor,
                  k_hi: torch.Tensor, dne: torch.Tensor, dt: float,
                  ws: torch.Tensor | None = None, flags: int = ionize.ION_F32,
                  conservation: bool = True, eps_shift: float = 1e-6,
                  degen_gap: float = 1e-3, surrogate: ionize.Surrogate | None = None,
-                 pop_tol: float = 1e-6):
+                 pop_tol: float = 1e-6, window: dict | None = None):
         if not fields:
             raise ValueError("at least one field")
         dev = N.device
@@ -62,10 +63,10 @@ class StepGraph:
             for s, E in enumerate(self.fields):
                 if surrogate is None:
                     ionize.step(sp, E, N, k_lo, k_hi, dt, dne, ws=self.ws, eps_shift=eps_shift,
-                                degen_gap=degen_gap, flags=flags)
+                                degen_gap=degen_gap, flags=flags, window=window)
                 else:
                     surrogate.step(E, N, k_lo, k_hi, dt, dne, ws=self.ws, eps_shift=eps_shift,
-                                   degen_gap=degen_gap, pop_tol=pop_tol)
+                                   degen_gap=degen_gap, pop_tol=pop_tol, window=window)
                 if conservation:
                     ionize.conservation(N, self.cons[s:s + 1], ncells=n)
         torch.cuda.current_stream(dev).wait_stream(side)
