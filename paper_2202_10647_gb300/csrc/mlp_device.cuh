@@ -47,9 +47,11 @@ __device__ __forceinline__ float bf16_round(float x) {
 // otherwise tanhf.
 template <bool Fast>
 __device__ __forceinline__ float gelu(float z, float& t) {
-  const float u = kGeluC * fmaf(kGeluA * z * z, z, z);
+  // u = c (z + a z^3) = z (c + c a z^2); g = z/2 + (z/2) t
+  const float u = z * fmaf(kGeluC * kGeluA, z * z, kGeluC);
   t = Fast ? tanh_approx(u) : tanhf(u);
-  return 0.5f * z * (1.0f + t);
+  const float hz = 0.5f * z;
+  return fmaf(hz, t, hz);
 }
 
 template <bool Fast>
