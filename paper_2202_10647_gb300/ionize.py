@@ -215,8 +215,10 @@ def _stream(t: torch.Tensor):
     return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
-def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+def _ptr(t, offset: int = 0):
+    """Device address of element `offset` (along the last axis for the
+    population planes, which keep their stride ld)."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr() + offset * t.element_size())
 
 
 def _need(t: torch.Tensor, name: str, dtype, device=None):
@@ -305,10 +307,13 @@ def step(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
          k_hi: torch.Tensor, dt: float, dne: torch.Tensor,
          n_gas: torch.Tensor | None = None, ws: torch.Tensor | None = None,
          eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32,
-         ncells: int | None = None, window: dict | None = None) -> torch.Tensor:
+         ncells: int | None = None, window: dict | None = None,
+         offset: int = 0) -> torch.Tensor:
     """One ion_step.  N is (Z+1, ld) and is updated in place, as are k_lo and
     k_hi; dne is written.  window: None (the paper's slide) or
-    {"w_min": .., "w_max": .., "eps_grow": ..} for ION_WINDOW_ADAPTIVE.  Returns the workspace (its header holds the
+    {"w_min": .., "w_max": .., "eps_grow": ..} for ION_WINDOW_ADAPTIVE.
+    offset, ncells: step cells [offset, offset + ncells) of the arrays (the
+    planes keep their stride).  Returns the workspace (its header holds the
     counters described in include/ionize.h)."""
     f64 = bool(flags & ION_F64_PLAIN)
     dt_ = torch.float64 if f64 else torch.float32
@@ -322,15 +327,21 @@ def step(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tensor,
         _need(n_gas, "n_gas", dt_, dev)
     if N.dim() != 2 or N.shape[0] != sp.Z + 1:
         raise ValueError(f"N must have shape (Z+1, ld) = ({sp.Z + 1}, ld)")
-    n = E.numel() if ncells is None else int(ncells)
+    off = int(offset)
+    n = E.numel() - off if ncells is None else int(ncells)
+    if off < 0 or n < 0 or off + n > min(E.numel(), k_lo.numel(), k_hi.numel(),
+                                         dne.numel(), N.shape[1]):
+        raise ValueError("offset/ncells outside the arrays")
+    if n_gas is not None and off + n > n_gas.numel():
+        raise ValueError("offset/ncells outside n_gas")
     if ws is None:
         ws = workspace(n, flags, dev)
     _need(ws, "ws", torch.uint8, dev)
     opts = _opts(eps_shift, degen_gap, window)
-    _check(lib().ion_step(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
-                          _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
-                          ctypes.byref(opts), int(flags), _ptr(ws), ws.numel(),
-                          _stream(E)))
+    _check(lib().ion_step(sp.handle, _ptr(E, off), _ptr(N, off), N.shape[1], n,
+                          float(dt), _ptr(k_lo, off), _ptr(k_hi, off), _ptr(dne, off),
+                          _ptr(n_gas, off), ctypes.byref(opts), int(flags), _ptr(ws),
+                          ws.numel(), _stream(E)))
     return ws
 
 

@@ -370,3 +370,22 @@ def test_full_size_nitrogen_sampled():
     Ng = wl.N[:, idx].double().cpu().numpy()
     assert np.abs(Ng - No).max() <= 2e-6
     assert np.abs(dne[idx].double().cpu().numpy() - dneo).max() <= 1e-5
+
+
+def test_cell_ranges_with_offset():
+    """Stepping cell ranges through `offset` gives what one whole call gives
+    (ranges on 64-cell boundaries take the same kernel path)."""
+    wl = W.nitrogen_3d(8, 16, 64, device="cuda")
+    n = wl.ncells
+    sp = gpu_species(wl.species)
+    N1, lo1, hi1 = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
+    d1 = torch.zeros(n, device="cuda")
+    ionize.step(sp, wl.E, N1, lo1, hi1, 0.05, d1)
+    N2, lo2, hi2 = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
+    d2 = torch.zeros(n, device="cuda")
+    for c0 in range(0, n, 2048):
+        ionize.step(sp, wl.E, N2, lo2, hi2, 0.05, d2, offset=c0, ncells=min(2048, n - c0))
+    assert torch.equal(N1, N2) and torch.equal(lo1, lo2) and torch.equal(hi1, hi2)
+    assert torch.equal(d1, d2)
+    with pytest.raises(ValueError):
+        ionize.step(sp, wl.E, N2, lo2, hi2, 0.05, d2, offset=n - 10, ncells=20)
