@@ -268,6 +268,9 @@ int make_policy(double dt_fs, const ion_step_opts* opts, int flags, ion::Policy*
   pol->wmin = o.w_min;
   pol->wmax = o.w_max;
   pol->eps_grow = o.eps_grow;
+  pol->eps_f = (float)o.eps_shift;
+  pol->gap_f = (float)o.degen_gap;
+  pol->eps_grow_f = (float)o.eps_grow;
   return ION_OK;
 }
 

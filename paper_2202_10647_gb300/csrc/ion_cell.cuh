@@ -111,9 +111,10 @@ __device__ __forceinline__ void window_after_step(const JobIO& J, const Policy& 
                                                   const T (&v)[WM], int w, int& lo, int& hi) {
   if (pol.flags & ION_NO_WINDOW_UPDATE) return;
   if (pol.adaptive)
-    adapt_window<T, WM>(v, w, J.Z, (T)pol.eps, pol.wmin, pol.wmax, (T)pol.eps_grow, lo, hi);
-  else if (v[0] < (T)pol.eps && hi < J.Z)
-    slide_window<T, WM>(v, w, J.Z, (T)pol.eps, lo, hi);
+    adapt_window<T, WM>(v, w, J.Z, pol_eps<T>(pol), pol.wmin, pol.wmax, pol_grow<T>(pol), lo,
+                        hi);
+  else if (v[0] < pol_eps<T>(pol) && hi < J.Z)
+    slide_window<T, WM>(v, w, J.Z, pol_eps<T>(pol), lo, hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, i
       } else {
         if (allow_fb && (pol.flags & ION_NO_FP64_FALLBACK) == 0 &&
             ((pol.flags & ION_FORCE_FP64_COEF) != 0 ||
-             (pol.gap > 0.0 && near_degenerate<T, WM>(lam, w, (T)pol.gap))))
+             (pol.gap > 0.0 && near_degenerate<T, WM>(lam, w, pol_gap<T>(pol)))))
           return true;
         dne = dd_update<T, WM>(v, lam, w);
       }

@@ -201,6 +201,19 @@ __device__ constexpr double kThrF64[20] = {
     0.294354,  0.387859,    0.494882,    0.614969,    0.747572,   0.892092,
     1.04791,   1.21439};
 
+// 1/n! for n = 0..17 (the Taylor branch needs n <= 4 + 12), in each
+// precision (the FP32 path reads no double: conversions run on the FP64 pipe).
+__device__ constexpr double kInvFact[18] = {
+    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040,
+    1.0 / 40320, 1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600,
+    1.0 / 6227020800.0, 1.0 / 87178291200.0, 1.0 / 1307674368000.0,
+    1.0 / 20922789888000.0, 1.0 / 355687428096000.0};
+__device__ constexpr float kInvFactF[18] = {
+    1.0f, 1.0f, 1.0f / 2, 1.0f / 6, 1.0f / 24, 1.0f / 120, 1.0f / 720, 1.0f / 5040,
+    1.0f / 40320, 1.0f / 362880, 1.0f / 3628800, 1.0f / 39916800, 1.0f / 479001600,
+    1.0f / 6227020800.0f, 1.0f / 87178291200.0f, 1.0f / 1307674368000.0f,
+    1.0f / 20922789888000.0f, 1.0f / 355687428096000.0f};
+
 template <typename T>
 struct DDParams;
 
@@ -218,6 +231,7 @@ struct DDParams<float> {
     return R;
   }
   __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  __device__ static __forceinline__ float inv_fact(int n) { return kInvFactF[n]; }
 };
 
 template <>
@@ -234,6 +248,7 @@ struct DDParams<double> {
     return R;
   }
   __device__ static __forceinline__ double div(double a, double b) { return a / b; }
+  __device__ static __forceinline__ double inv_fact(int n) { return kInvFact[n]; }
 };
 
 __host__ __device__ constexpr int popc_c(int x) {
@@ -249,12 +264,7 @@ __host__ __device__ constexpr int range_mask(int j, int i) {
   return ((1 << (i + 1)) - 1) & ~((1 << j) - 1);
 }
 
-// 1/n! for n = 0..17 (the Taylor branch needs n <= 4 + 12).
-__device__ constexpr double kInvFact[18] = {
-    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040,
-    1.0 / 40320, 1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600,
-    1.0 / 6227020800.0, 1.0 / 87178291200.0, 1.0 / 1307674368000.0,
-    1.0 / 20922789888000.0, 1.0 / 355687428096000.0};
+
 
 // Taylor branch of dd_exp_all for the subset `mask` of the nodes z[0..n-1]
 // (n <= 5), without the factor e^{zmx}: sum_r h_r(z - zmx) / (m-1+r)!.
@@ -283,7 +293,7 @@ __device__ __noinline__ T dd_taylor(T z0, T z1, T z2, T z3, T z4, int mask,
   T acc = T(0);
 #pragma unroll
   for (int r = 0; r <= P::RMAX; ++r)
-    if (r <= R) acc = fma(H[r], T(kInvFact[m - 1 + r]), acc);
+    if (r <= R) acc = fma(H[r], P::inv_fact(m - 1 + r), acc);
   return acc;
 }
 

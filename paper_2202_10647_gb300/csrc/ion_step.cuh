@@ -48,7 +48,28 @@ struct Policy {
   int adaptive;     // ION_WINDOW_ADAPTIVE
   int wmin, wmax;   // adaptive widths
   double eps_grow;  // adaptive: the top grows above this population
+  float eps_f, gap_f, eps_grow_f;  // the same in FP32 (no per-cell conversion)
 };
+
+// eps, gap, eps_grow of the policy in the precision of the caller.
+template <typename T>
+__device__ __forceinline__ T pol_eps(const Policy& p);
+template <>
+__device__ __forceinline__ float pol_eps<float>(const Policy& p) { return p.eps_f; }
+template <>
+__device__ __forceinline__ double pol_eps<double>(const Policy& p) { return p.eps; }
+template <typename T>
+__device__ __forceinline__ T pol_gap(const Policy& p);
+template <>
+__device__ __forceinline__ float pol_gap<float>(const Policy& p) { return p.gap_f; }
+template <>
+__device__ __forceinline__ double pol_gap<double>(const Policy& p) { return p.gap; }
+template <typename T>
+__device__ __forceinline__ T pol_grow(const Policy& p);
+template <>
+__device__ __forceinline__ float pol_grow<float>(const Policy& p) { return p.eps_grow_f; }
+template <>
+__device__ __forceinline__ double pol_grow<double>(const Policy& p) { return p.eps_grow; }
 
 // Workspace views.
 struct Scratch {

@@ -234,10 +234,10 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     for (int r = 0; r < WM; ++r) v[j][r] += inc[j][r];
     if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0) {
       if constexpr (AD)
-        adapt_window<float, WM>(v[j], w[j], J.Z, (float)pol.eps, pol.wmin, pol.wmax,
-                                (float)pol.eps_grow, nlo[j], nhi[j]);
-      else if (v[j][0] < (float)pol.eps && hi[j] < J.Z)
-        slide_window<float, WM>(v[j], w[j], J.Z, (float)pol.eps, nlo[j], nhi[j]);
+        adapt_window<float, WM>(v[j], w[j], J.Z, pol.eps_f, pol.wmin, pol.wmax,
+                                pol.eps_grow_f, nlo[j], nhi[j]);
+      else if (v[j][0] < pol.eps_f && hi[j] < J.Z)
+        slide_window<float, WM>(v[j], w[j], J.Z, pol.eps_f, nlo[j], nhi[j]);
     }
   }
   // stores
@@ -511,14 +511,17 @@ __global__ void __launch_bounds__(W * 32)
   }
 }
 
-// The stiff-cell records, one per thread.
+// The stiff-cell records, one per thread.  W bounds the width; the window
+// planes past the cell's own width are zero.
 template <int W>
 __device__ __forceinline__ bool record_cell(const BatchArgs& a, const StagedF32& tab,
                                             const JobIO& J, int64_t i, int c, float Ec,
                                             int lo, int hi) {
   float v[W];
 #pragma unroll
-  for (int r = 0; r < W; ++r) v[r] = __ldcs(a.ws.rec_V + (int64_t)r * a.ws.rec_cap + i);
+  const int w = hi - lo + 1;
+  for (int r = 0; r < W; ++r)
+    v[r] = r < w ? __ldcs(a.ws.rec_V + (int64_t)r * a.ws.rec_cap + i) : 0.0f;
   return finish_cell<F32Form, W>(J, a.pol, tab, c, Ec, lo, hi, v, true);
 }
 
@@ -532,35 +535,31 @@ __global__ void __launch_bounds__(256)
   const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
     bool fb = false;
-    int c = 0, jid = 0;
+    int c = 0, jid = 0, lo = 0, hi = -1;
+    float Ec = 0.0f;
     if (i < n) {
       c = (int)__ldcs(a.ws.rec_c + i);
       jid = a.ws.rec_job[i];
-      const JobIO& J = a.job[jid];
-      const float Ec = __ldcs(a.ws.rec_E + i);
+      Ec = __ldcs(a.ws.rec_E + i);
       const unsigned lh = __ldcs(a.ws.rec_lohi + i);
-      const int lo = lh & 0xff, hi = lh >> 8;
+      lo = lh & 0xff;
+      hi = lh >> 8;
+    }
+    // the warp's widest window picks one of three width bounds for all its
+    // lanes (fewer code paths, no divergence by width)
+    const int wl = hi - lo + 1;
+    const int Wm = __reduce_max_sync(kFull, wl);
+    if (wl >= 1) {
+      const JobIO& J = a.job[jid];
       const StagedF32& tab = tabs[jid];
-      switch (hi - lo + 1) {
-        case 1:
-          fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi);
-          break;
-        case 2:
-          fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi);
-          break;
-        case 3:
-          fb = record_cell<3>(a, tab, J, i, c, Ec, lo, hi);
-          break;
-        case 4:
-          fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi);
-          break;
-        case 5:
-          fb = record_cell<5>(a, tab, J, i, c, Ec, lo, hi);
-          break;
-        default:
-          fb = record_cell<6>(a, tab, J, i, c, Ec, lo, hi);
-          break;
-      }
+      if (wl == 1)
+        fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi);
+      else if (Wm <= 2)
+        fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi);
+      else if (Wm <= 4)
+        fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi);
+      else
+        fb = record_cell<6>(a, tab, J, i, c, Ec, lo, hi);
     }
     warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb, (uint32_t)c,
                 (uint8_t)jid);

@@ -1,12 +1,14 @@
 """Run a few steps on a reduced copy of a benchmark workload, for profilers.
 
   python -m paper_2202_10647_gb300.profile_step [--nz 64]
-        [--form f32|f64|both|surrogate] [--steps 3] [--train-steps 1000]
+        [--form f32|f64|both|surrogate|argon] [--steps 3] [--train-steps 1000]
 
 f32/f64: the nitrogen 3D workload on nz x 256 x 512 cells (x fastest) of the
 256 x 256 x 512 benchmark's recipe (a few GB of device memory at most for
-nz <= 64).  surrogate: the Ar-like lognormal workload on as many cells, with
-a surrogate trained for --train-steps steps, stepped by ion_step_surrogate.
+nz <= 64).  argon: the Ar-like lognormal workload (the mixed-batch and
+surrogate recipe) on as many cells, stepped by ion_step (FP32).  surrogate:
+the same cells with a surrogate trained for --train-steps steps, stepped by
+ion_step_surrogate.
 Every step starts from the same input state.  Meant to be wrapped by ncu
 with a kernel filter and a launch count, e.g.
   ncu --set full --clock-control none -k regex:ion_stream_kernel -s 1 -c 1 ...
@@ -21,11 +23,29 @@ from . import ionize, workloads
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nz", type=int, default=64)
-    ap.add_argument("--form", default="both", choices=["f32", "f64", "both", "surrogate"])
+    ap.add_argument("--form", default="both",
+                    choices=["f32", "f64", "both", "surrogate", "argon"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--train-steps", type=int, default=1000)
     args = ap.parse_args()
     dev = torch.device("cuda")
+    if args.form == "argon":
+        sd = workloads.argon_like()
+        sp = ionize.Species(sd.U, sd.l, sd.m)
+        wl = workloads.ladder_cells(sd, args.nz * 256 * 512, 4, device=dev)
+        n = wl.ncells
+        N0, lo0, hi0 = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
+        dne = torch.empty(n, device=dev)
+        ws = ionize.workspace(n)
+        for _ in range(args.steps):
+            wl.N.copy_(N0)
+            wl.lo.copy_(lo0)
+            wl.hi.copy_(hi0)
+            ionize.step(sp, wl.E, wl.N, wl.lo, wl.hi, 0.05, dne, ws=ws)
+        torch.cuda.synchronize()
+        print("argon: fp64-coefficient cells, invalid windows:", ionize.counters(ws),
+              "stiff cells:", ionize.stiff_cells(ws), "of", n)
+        return
     if args.form == "surrogate":
         from . import surrogate
         sd = workloads.argon_like()
