@@ -189,9 +189,10 @@ struct StepArgs {
 };
 
 // Taylor-form update of one cell whose rates all have W dt <= 1 (w <= 6,
-// the window's populations loaded here): the same series, window slide and
-// stores as ion_step's streaming kernel.
+// v its window's populations, zero past w): the same series, window slide
+// and stores as ion_step's streaming kernel.
 __device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, int hi,
+                                            float (&v)[ION_MAX_WINDOW],
                                             const float (&lam)[ION_MAX_WINDOW], float lmax) {
   const JobIO& J = a.J;
   float* __restrict__ N = static_cast<float*>(J.N);
@@ -199,13 +200,6 @@ __device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, in
   float dne = 0.0f;
   int nlo = lo, nhi = hi;
   if (w >= 2) {
-    float v[ION_MAX_WINDOW];
-    const float* p = N + (int64_t)lo * J.ld + c;
-#pragma unroll
-    for (int r = 0; r < ION_MAX_WINDOW; ++r) {
-      v[r] = r < w ? __ldcs(p) : 0.0f;
-      p += J.ld;
-    }
     dne = taylor_propagate<float, ION_MAX_WINDOW>(v, lam, w, lmax);
     window_after_step<float, ION_MAX_WINDOW>(J, a.pol, v, w, nlo, nhi);
     float* q = N + (int64_t)lo * J.ld + c;
@@ -296,6 +290,28 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
     }
     __syncthreads();  // every thread is done with the previous tile's Y
     const float Eabs = on ? fabsf(a.E[c]) : 1.0f;
+    // the step's window populations, loaded now so that the loads are in
+    // flight while the network is evaluated
+    int clo = 0, chi = 0;
+    bool valid = false;
+    float v[ION_MAX_WINDOW];
+#pragma unroll
+    for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = 0.0f;
+    if constexpr (Step) {
+      if (on) {
+        clo = a.J.lo[c];
+        chi = a.J.hi[c];
+        valid = window_ok(clo, chi, a.J.Z);
+        if (valid) {
+          const float* p = static_cast<const float*>(a.J.N) + (int64_t)clo * a.J.ld + c;
+#pragma unroll
+          for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+            if (r < chi - clo + 1) v[r] = __ldcs(p);
+            p += a.J.ld;
+          }
+        }
+      }
+    }
     const bool pos = Eabs > (float)kEmin && Eabs < INFINITY;
     const float l2 = log2f(pos ? Eabs : 1.0f);
     const float x = fminf(fmaxf(fmaf(K.xa, l2, K.xb), -1.0f), 1.0f);
@@ -387,15 +403,8 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
           a.W_out[(int64_t)k * a.ldw + c] = s < K.yfloor ? 0.0f : exp2f(s);
         }
     } else {
-      const JobIO& J = a.J;
-      int lo = 0, hi = 0;
-      bool valid = false;
-      if (on) {
-        lo = J.lo[c];
-        hi = J.hi[c];
-        valid = window_ok(lo, hi, J.Z);
-        if (!valid) atomicAdd(&a.ws.hdr[kHdrInvalid], 1u);
-      }
+      const int lo = clo, hi = chi;
+      if (on && !valid) atomicAdd(&a.ws.hdr[kHdrInvalid], 1u);
       const int w = hi - lo + 1;
       float lam[ION_MAX_WINDOW];
 #pragma unroll
@@ -437,17 +446,9 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
       plain = plain || stiff;
       warp_count(&a.ws.hdr[kHdrSurrogate], net);
       warp_count(&a.ws.hdr[kHdrPlain], plain);
-      if (__ballot_sync(kFull, stiff)) {
-        float vin[ION_MAX_WINDOW];
-        const float* p = static_cast<const float*>(J.N) + (int64_t)lo * J.ld + c;
-#pragma unroll
-        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
-          vin[r] = (stiff && r < w) ? __ldcs(p) : 0.0f;
-          p += J.ld;
-        }
-        append_record(a.ws, stiff, 0, (int)c, on ? a.E[c] : 0.0f, lo, hi, vin);
-      }
-      if (valid && !stiff) taylor_cell(a, (int)c, lo, hi, lam, lmax);
+      if (__ballot_sync(kFull, stiff))
+        append_record(a.ws, stiff, 0, (int)c, on ? a.E[c] : 0.0f, lo, hi, v);
+      if (valid && !stiff) taylor_cell(a, (int)c, lo, hi, v, lam, lmax);
     }
   }
   // leave: tensor memory is freed by the warp that allocated it once every
