@@ -105,9 +105,9 @@ __global__ void rates_f64_kernel(const ion::SpeciesTable* t, const double* E,
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
-  const double e = E[c];
+  const ion::FieldF64 f = ion::field_f64(E[c]);
   for (int k = k_lo; k < k_hi; ++k)
-    W[(int64_t)(k - k_lo) * ldw + c] = ion::rate_dt_f64(tab, k, e);
+    W[(int64_t)(k - k_lo) * ldw + c] = ion::rate_dt_f64(tab, k, f);
 }
 
 int check_species(const ion_species* sp) {

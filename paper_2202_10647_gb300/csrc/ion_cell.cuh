@@ -53,12 +53,10 @@ struct F32Form {
 struct F64Form {
   using T = double;
   using Staged = StagedF64;
-  struct Field {
-    double E;
-  };
-  __device__ static Field field(double E) { return {E}; }
+  using Field = FieldF64;
+  __device__ static Field field(double E) { return field_f64(E); }
   __device__ static double rate(const StagedF64& t, int k, const Field& f) {
-    return rate_dt_f64(t, k, f.E);
+    return rate_dt_f64(t, k, f);
   }
 };
 

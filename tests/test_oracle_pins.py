@@ -170,6 +170,39 @@ def test_expm_vs_arbitrary_precision(lam):
     assert np.max(np.abs(got[nz] - want[nz]) / want[nz]) <= 1e-12
 
 
+def uniformized_expm(A):
+    """exp(A) for a generator A (off-diagonal >= 0, columns summing to 0) by
+    uniformization (Jensen): with q >= max |A_ii| and P = I + A/q, exp(A) =
+    e^{-q} sum_n q^n/n! P^n.  P is column-stochastic, so every term is
+    non-negative and nothing cancels.  Large q is split into m substeps,
+    each done this way, and the results multiplied."""
+    w = A.shape[0]
+    q = max(1e-300, float(np.max(-np.diag(A))))
+    m = max(1, int(math.ceil(q / 20.0)))
+    qs = q / m
+    P = np.eye(w) + A / q
+    term = np.eye(w) * math.exp(-qs)
+    X = term.copy()
+    n = 0
+    while True:
+        n += 1
+        term = term @ P * (qs / n)
+        X += term
+        if n > qs and term.max() < 1e-20:
+            break
+    return np.linalg.matrix_power(X, m)
+
+
+@pytest.mark.parametrize("lam", LAM_CASES)
+def test_expm_vs_uniformization(lam):
+    A = window_matrix(lam)
+    got = oracle.expm(A)
+    want = uniformized_expm(A)
+    # the m substep products of the uniformization round about m times
+    m = max(1, int(math.ceil(float(np.max(-np.diag(A))) / 20.0)))
+    assert np.max(np.abs(got - want)) <= 2e-15 * (m + 10)
+
+
 def test_expm_equal_rate_closed_forms():
     # Equal rates lam, unit population at the bottom: N_j = lam^j e^-lam / j!
     # below the absorbing top (Poisson), the top gets the rest.
