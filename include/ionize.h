@@ -408,8 +408,9 @@ ION_API int ion_surrogate_rates(const ion_surrogate* s, const float* E, int64_t 
  * give a bound on the population error of the step,
  *   2 dt sum_r (max(W_r, 2^y_floor) (2^bound - 1) + 2^y_floor)
  * (a perturbation of the rate matrix by dA moves the solution of Eq. 3 by
- * at most |dA| in the 1-norm); if it is at most pop_tol the network's rates
- * are used, otherwise (and outside the range) the rates of Eq. 1.  A cell
+ * at most |dA| in the 1-norm); if it is below pop_tol the network's rates
+ * are used, otherwise (and outside the range) the rates of Eq. 1; pop_tol 0
+ * never uses the network.  A cell
  * with some rate W dt > 1 always takes the rates of Eq. 1 (its bound would
  * exceed any useful tolerance) and is finished in the Bateman form by
  * ion_step's record kernel.  The update itself is ion_step's (Taylor or

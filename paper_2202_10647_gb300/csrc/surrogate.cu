@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
             err += 2.0f * fmaf(fmaxf(lam[r], wfloor), beta, wfloor);
           }
         }
-        net = in_range && err <= a.pop_tol;
+        net = in_range && err < a.pop_tol;  // pop_tol 0: never the network
         if (!net) {
           plain = true;
           const FieldF32 f = field_f32(a.E[c]);
