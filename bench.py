@@ -86,6 +86,28 @@ def recorded_traffic():
         return None
 
 
+# ---------------------------------------------------------------------------
+# multi-rank host logic (one process per GPU, weak scaling, no data-path
+# collective): every rank steps its own full-size shard
+# ---------------------------------------------------------------------------
+def shard_seed(rank: int) -> int:
+    """Seed of rank `rank`'s shard of the workload (shards differ)."""
+    return 2 + rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks of the default process group."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def job_value(world: int, cells_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job cell-updates/s: every rank's cells over the slowest rank's time."""
+    return world * cells_per_rank * steps / (total_ms * 1e-3)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -232,7 +254,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     # -- inputs (resident in HBM before timing starts) ----------------------
-    wl = W.nitrogen_3d(*GRID, seed=2 + rank, device=dev)
+    wl = W.nitrogen_3d(*GRID, seed=shard_seed(rank), device=dev)
     n = wl.ncells
     sp = ionize.Species(wl.species.U, wl.species.l, wl.species.m)
     N0, lo0, hi0 = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
@@ -287,12 +309,10 @@ def main():
     stiff = ionize.stiff_cells(ws)
     total_ms = float(sum(t_step))
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
+        total_ms = max_over_ranks(total_ms, dist, dev)
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = job_value(world, n, args.steps, total_ms)
     # the roofline is taken over the whole step (its three kernels and the
     # counter reset): algorithmic bytes of one step / measured step time
     main_ms = float(np.mean(t_step))
