@@ -349,6 +349,10 @@ def main():
     torch.cuda.synchronize()
     ms64 = float(np.mean([a.elapsed_time(b) for a, b in ev64]))
     bytes64 = int(W.window_bytes_per_cell(lo0, hi0, elem=8).sum())
+    # the FP64 form is bound by FP64 transcendentals: per cell one log2 and
+    # one exp2 per window rate (w-1), against the measured FP64 exp2 rate
+    pk = ionize.measure_peaks()
+    trans64 = float((w.double() - 1.0).clamp(min=0).sum() + n)
     # FP64 vs FP32 outputs on the same inputs (one step each)
     restore64()
     step_f64()
@@ -712,12 +716,19 @@ def main():
                                   "fp64_coefficient_cells": fb_cells,
                                   "second_kernel_cells": stiff},
             "fp64_plain": {"value": n / (ms64 * 1e-3), "ms_per_step": ms64,
-                           "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9},
+                           "achieved_GBs": bytes64 / (ms64 * 1e-3) / 1e9,
+                           "roofline": {"bound": "alu",
+                                        "achieved": trans64 / (ms64 * 1e-3),
+                                        "peak": pk["fp64_exp2_per_s"],
+                                        "unit": "FP64 exp2-class evaluations/s",
+                                        "frac": trans64 / (ms64 * 1e-3) / pk["fp64_exp2_per_s"],
+                                        "peak_source": "measured (ion_measure_peaks)"}},
             "batched_mixed_species": batched,
             "krypton_beams_50_steps_graph": krypton,
             "surrogate_argon": surrogate,
         },
         "accuracy": acc,
+        "peaks_measured": pk,
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -428,6 +428,15 @@ ION_API int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N,
                                double pop_tol, void* workspace, size_t workspace_bytes,
                                void* stream);
 
+/* ion_measure_peaks -- throughput of the current device for the arithmetic
+ * the step's forms are bound by, from loops of independent dependency chains
+ * over all SMs: out[0] FP32 ex2 (SFU) per second, out[1] FP32 tanh (SFU) per
+ * second, out[2] FP64 flop/s of fused multiply-adds, out[3] FP64 exp2 per
+ * second.  A measurement utility: it allocates 64 bytes, creates events and
+ * synchronizes (about 0.1 s).  The paper has no counterpart.
+ * Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_measure_peaks(double* out);
+
 /* Message of the last failed call on this thread ("" if none). */
 ION_API const char* ion_last_error(void);
 

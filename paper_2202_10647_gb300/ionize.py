@@ -40,7 +40,7 @@ EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
            "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
            "ion_surrogate_create", "ion_surrogate_destroy", "ion_surrogate_rates",
-           "ion_step_surrogate", "ion_last_error")
+           "ion_step_surrogate", "ion_measure_peaks", "ion_last_error")
 
 #: forward pass in the tensor-core arithmetic (bf16 W2, W3, h1, h2; SFU tanh)
 ION_MLP_BF16 = 0x1
@@ -182,6 +182,8 @@ def _declare(lib):
     lib.ion_step_surrogate.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                        _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_double,
                                        _vp, ctypes.c_size_t, _vp]
+    lib.ion_measure_peaks.restype = ctypes.c_int
+    lib.ion_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.ion_step_noalloc.restype = ctypes.c_int
     lib.ion_step_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                      _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp]
@@ -616,3 +618,11 @@ def surrogate_counters(ws: torch.Tensor):
     of the last ion_step_surrogate that used `ws` (synchronizes)."""
     h = ws[:24].cpu().view(torch.int32)
     return int(h[3]), int(h[4]), int(h[5])
+
+
+def measure_peaks() -> dict:
+    """ion_measure_peaks on the current device (synchronizes)."""
+    out = (ctypes.c_double * 4)()
+    _check(lib().ion_measure_peaks(out))
+    return {"sfu_ex2_per_s": out[0], "sfu_tanh_per_s": out[1], "fp64_flops": out[2],
+            "fp64_exp2_per_s": out[3]}
