@@ -108,6 +108,17 @@ def job_value(world: int, cells_per_rank: int, steps: int, total_ms: float) -> f
     return world * cells_per_rank * steps / (total_ms * 1e-3)
 
 
+def bf16_peak() -> float:
+    """Dense bf16 TFLOP/s: MEASURED_PEAKS.json (burst), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"])
+    return 1900.0
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -495,6 +506,19 @@ def main():
                      "train": {"seconds": train_s, "steps": tr4.steps, "pairs": 1 << 20,
                                "final_loss": tr4.losses[-1][1]},
                      "pop_tol": 1e-6,
+                     # the network's work per cell: 128 GELUs (one SFU tanh
+                     # each) and 2 (64*64 + 64*32) bf16 tensor flops
+                     "roofline": {
+                         "bound": "alu",
+                         "achieved": 128 * n4 / (t_net4 * 1e-3),
+                         "peak": pk["sfu_tanh_per_s"],
+                         "unit": "SFU tanh/s",
+                         "frac": 128 * n4 / (t_net4 * 1e-3) / pk["sfu_tanh_per_s"],
+                         "peak_source": "measured (ion_measure_peaks)",
+                         "tensor_TFLOPs": 2 * (64 * 64 + 64 * 32) * n4 / (t_net4 * 1e-3) / 1e12,
+                         "tensor_frac_of_bf16_peak": 2 * (64 * 64 + 64 * 32) * n4
+                         / (t_net4 * 1e-3) / 1e12 / bf16_peak(),
+                         "note": "whole surrogate step (network kernel + record kernel)"},
                      "cells_on_network_rates": n_net4 / n4,
                      "cells_on_eq1_rates": n_plain4 / n4, "timeouts": tmo4,
                      "accuracy": acc4}
