@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2202_10647_gb300 import ionize, workloads as W
 from test_gpu_step import check, oracle_species
 
@@ -86,3 +87,36 @@ def test_batched_rejects_bad_arguments():
         ionize.step_batched(jobs, 0.05, shape=(3, 4, 0))
     with pytest.raises(ValueError):
         ionize.step_batched(jobs * 3, 0.05)
+
+
+def test_full_size_mixed_batch_sampled():
+    """The mixed-species workload at its benchmark size (N 20M, Ar-like 8M,
+    Kr-like 2M cells) in the autotuned launch shape: sampled cells of every
+    species against the oracle, conservation over every cell."""
+    dev = "cuda"
+    wls = W.mixed_batch(scale=1.0, seed=3, device=dev)
+    sps = [ionize.Species(w.species.U, w.species.l, w.species.m) for w in wls]
+    dnes = [torch.empty(w.ncells, device=dev) for w in wls]
+    jobs = [(sp, w.E, w.N, w.lo, w.hi, d) for sp, w, d in zip(sps, wls, dnes)]
+    ws = ionize.batched_workspace(jobs)
+    pristine = [(w.N.clone(), w.lo.clone(), w.hi.clone()) for w in wls]
+    shape, _ = ionize.autotune(jobs, 0.05, ws=ws, reps=2)
+    for w, (n0, l0, h0) in zip(wls, pristine):
+        w.N.copy_(n0)
+        w.lo.copy_(l0)
+        w.hi.copy_(h0)
+    rng = np.random.default_rng(11)
+    samples = []
+    for w in wls:
+        ix = torch.tensor(np.sort(rng.choice(w.ncells, 3000, replace=False)), device=dev)
+        samples.append((ix, w.E[ix].double().cpu().numpy(), w.N[:, ix].double().cpu().numpy(),
+                        w.lo[ix].cpu().numpy(), w.hi[ix].cpu().numpy()))
+    ionize.step_batched(jobs, 0.05, ws=ws, shape=shape)
+    torch.cuda.synchronize()
+    for w, (n0, _, _), (ix, Es, Ns, ls, hs) in zip(wls, pristine, samples):
+        n = w.ncells
+        tot = (w.N[:, :n].double().sum(0) - n0[:, :n].double().sum(0)).abs().max()
+        assert float(tot) <= 1e-6
+        No, loo, hio, dneo = oracle.step(oracle_species(w.species), Es, Ns, 0.05, ls, hs)
+        err = np.abs(w.N[:, ix].double().cpu().numpy() - No).max()
+        assert err <= 2e-6, (w.species.name, err)

@@ -207,3 +207,25 @@ def test_surrogate_gain(argon_net):
     print(f"plain FP32 {t_plain:.3f} ms, surrogate {t_net:.3f} ms "
           f"(gain {t_plain / t_net:.2f}x); network rates for {n_net / n:.1%} of the cells")
     assert t_net > 0 and t_plain > 0
+
+
+def test_full_size_surrogate_sampled(argon_net):
+    """The surrogate form on the 33.5M-cell Ar-like workload: sampled cells
+    within the FP32 bar of the oracle, conservation over every cell."""
+    sd, sp, net, tr, bound = argon_net
+    dev = "cuda"
+    wl = W.ladder_cells(sd, 33_554_432, 4, device=dev)
+    n = wl.ncells
+    rng = np.random.default_rng(12)
+    ix = torch.tensor(np.sort(rng.choice(n, 4000, replace=False)), device=dev)
+    Es, Ns = wl.E[ix].double().cpu().numpy(), wl.N[:, ix].double().cpu().numpy()
+    ls, hs = wl.lo[ix].cpu().numpy(), wl.hi[ix].cpu().numpy()
+    tot0 = wl.N[:, :n].double().sum(0)
+    dne = torch.empty(n, device=dev)
+    ws = net.step(wl.E, wl.N, wl.lo, wl.hi, 0.05, dne)
+    torch.cuda.synchronize()
+    n_net, n_plain, timeout = ionize.surrogate_counters(ws)
+    assert timeout == 0 and n_net > 0
+    assert float((wl.N[:, :n].double().sum(0) - tot0).abs().max()) <= 1e-6
+    No, _, _, _ = oracle.step(oracle_species(sd), Es, Ns, 0.05, ls, hs)
+    assert np.abs(wl.N[:, ix].double().cpu().numpy() - No).max() <= 2e-6
