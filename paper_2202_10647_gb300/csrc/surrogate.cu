@@ -315,6 +315,16 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
     const bool pos = Eabs > (float)kEmin && Eabs < INFINITY;
     const float l2 = log2f(pos ? Eabs : 1.0f);
     const float x = fminf(fmaxf(fmaf(K.xa, l2, K.xb), -1.0f), 1.0f);
+    // the step skips the network for a tile none of whose cells could use
+    // it (field outside the trained range, no rate in the window, or the
+    // network never trusted); the decision is uniform over the CTA
+    bool use_net = true;
+    if constexpr (Step) {
+      const bool mine = valid && chi > clo && pos && l2 >= K.l2lo && l2 <= K.l2hi &&
+                        !a.pol.zero_dt && a.pop_tol > 0.0f;
+      use_net = __syncthreads_or(mine) != 0;
+    }
+    if (use_net) {
     // layer 1 -> A row t
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -396,6 +406,7 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
       }
     }
     tc_fence_before();
+    }  // use_net
     if constexpr (!Step) {
       if (on)
         for (int k = 0; k < Z; ++k) {
@@ -411,14 +422,14 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
       for (int r = 0; r < ION_MAX_WINDOW; ++r) lam[r] = 0.0f;
       bool net = false, plain = false;
       if (valid && w >= 2 && !a.pol.zero_dt) {
-        const bool in_range = pos && l2 >= K.l2lo && l2 <= K.l2hi;
+        const bool in_range = use_net && pos && l2 >= K.l2lo && l2 <= K.l2hi;
         int bin = (int)floorf(fmaf(K.bin_a, l2, K.bin_b));
         bin = min(max(bin, 0), K.nbins - 1);
         const float wfloor = exp2f(K.yfloor + log2dt);
         float err = 0.0f;
 #pragma unroll
         for (int r = 0; r < ION_MAX_WINDOW - 1; ++r) {
-          if (r < w - 1) {
+          if (in_range && r < w - 1) {
             const int k = lo + r;
             const float s = Y[k * kM + t];
             lam[r] = s < K.yfloor ? 0.0f : ex2_approx(s + log2dt);
