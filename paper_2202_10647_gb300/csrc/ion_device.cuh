@@ -34,9 +34,14 @@ constexpr double kEmin = 1e-6;
 
 // FP32 copy of the table staged in shared memory, each double held as an
 // unevaluated sum hi + lo of two floats, with log2(dt) folded into a.
+// Entries Z.. are padding (never staged): a window's slots past its top
+// may index them, and their rates are masked.  ecold[k] (staged by the
+// streaming kernel only): a field strength below which W_j dt < 2^kColdLog2
+// for every j >= k, 0 where none was found safely.
 struct StagedF32 {
-  float4 hi[ION_MAX_Z + 1];  // {a_hi, b_hi, C_hi, a_lo}: one 16-byte load
-  float2 lo[ION_MAX_Z + 1];  // {b_lo, C_lo}
+  float4 hi[ION_MAX_Z + ION_MAX_WINDOW];  // {a_hi, b_hi, C_hi, a_lo}: one 16-byte load
+  float2 lo[ION_MAX_Z + ION_MAX_WINDOW];  // {b_lo, C_lo}
+  float ecold[ION_MAX_Z + ION_MAX_WINDOW];
 };
 
 struct StagedF64 {
@@ -111,6 +116,65 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// W dt below 2^kColdLog2 (9.3e-10) is far under the 1.5e-9 at which the FP32
+// Taylor series takes its first term (2 W dt > kThrF32[0]).
+constexpr float kColdLog2 = -30.0f;
+
+// Field strength E_c below which y(E) = a - b log2 E - C/E, the log2 of W dt
+// (Eq. 1), lies under kColdLog2; 0 when no such bound is found safely.  With
+// u = log2 E, g(u) = y - kColdLog2 is concave in u (g'' = -C ln^2 2 2^-u), so
+// Newton's iterates that start where g' > 0 approach the root from below
+// after their first step.  E_c is the last iterate less 2^-8 relative:
+// g(log2 E_c) <= about -0.25, margin for the FP32 arithmetic here and for
+// the FP32 rate evaluation that E_c stands in for.  Below the root g
+// increases with u, so every E < E_c has y < kColdLog2 as well.
+__device__ __forceinline__ float cold_field(double a_d, double b_d, double C_d) {
+  const float am = (float)a_d - kColdLog2, b = (float)b_d, C = (float)C_d;
+  constexpr float kLn2 = 0.693147181f;
+  // the start u0 = log2(C / am) has g'(u0) = am ln 2 - b; demand a margin
+  if (!(C > 0.0f) || !(am * kLn2 > b + 1.0f) || !(am < 1e30f)) return 0.0f;
+  float u = __log2f(__fdividef(C, am));
+  for (int i = 0; i < 12; ++i) {
+    const float e = C * ex2_approx(-u);
+    const float gp = fmaf(e, kLn2, -b);
+    if (!(gp > 0.0f)) return 0.0f;
+    u -= __fdividef(am - b * u - e, gp);
+  }
+  const float g = am - b * u - C * ex2_approx(-u);
+  if (!(g <= 0.01f) || !(u < 126.0f)) return 0.0f;
+  return ex2_approx(u) * (1.0f - 1.0f / 256.0f);
+}
+
+// One warp: ecold of one species (threads k < Z of the table in two rounds
+// of 32), each state's own cold field turned into the minimum over the
+// states at or above it by a suffix scan; the padding past Z holds 0 (never
+// cold).
+__device__ __forceinline__ void stage_cold_f32(const SpeciesTable* t, double log2dt,
+                                               StagedF32* s, int lane) {
+  const int Z = t->Z;
+  const float kInf = __int_as_float(0x7f800000);
+  float m[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = lane + 32 * h;
+    m[h] = k < Z ? cold_field(t->a2[k] + log2dt, t->b[k], t->C[k]) : kInf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float x = __shfl_down_sync(0xffffffffu, m[h], o);
+      if (lane + o < 32) m[h] = fminf(m[h], x);
+    }
+  }
+  m[0] = fminf(m[0], __shfl_sync(0xffffffffu, m[1], 0));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = lane + 32 * h;
+    s->ecold[k] = k < Z ? m[h] : 0.0f;
+  }
+  if (lane + 64 < ION_MAX_Z + ION_MAX_WINDOW) s->ecold[lane + 64] = 0.0f;
+}
+
+
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;

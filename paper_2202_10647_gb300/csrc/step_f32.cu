@@ -3,12 +3,14 @@
 // small kernels over the cells it left behind.
 //
 //   ion_stream_kernel<Q, W>  every warp walks its own sequence of chunks of
-//       32*Q cells (Q consecutive cells per lane) through a 3-stage ring in
-//       shared memory.  cp.async brings |E|, k_lo and k_hi in two chunks
-//       ahead and each lane's own window planes one chunk ahead (one copy of
+//       32*Q cells (Q consecutive cells per lane) through a 4-stage ring in
+//       shared memory.  cp.async brings |E|, k_lo and k_hi in three chunks
+//       ahead and each lane's own window planes two chunks ahead (one copy of
 //       4*Q bytes per plane when the lane's cells share their window), so the
 //       loads in flight cost no registers and the traffic is exactly the
-//       cells' windows.  A cell whose rates all have W dt <= 1 is finished
+//       cells' windows.  A chunk whose cells all lie below their species'
+//       cold field (no rate reaches the first Taylor term) only writes dne.
+//       A cell whose rates all have W dt <= 1 is finished
 //       here with the Taylor series of exp(dt A).  The others ("stiff" cells,
 //       the Bateman form) write the inputs already loaded into a record queue:
 //       in a laser field |E| swings from zero to its peak every few cells, so
@@ -34,7 +36,7 @@ namespace ion {
 
 namespace {
 
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 // The streaming kernel finishes every cell whose rates all have
 // W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[16].
 constexpr float kLamEasy = 1.0f;
@@ -130,13 +132,14 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 // 10^3, i.e. a relative error of W dt below 4e-5, which moves populations by
 // at most 4e-5 W dt; rates above kLamPrecise = 2^-6 (where that could reach
 // 6e-7) are recomputed in float-float.  The Taylor series runs the warp's
-// largest term count (extra terms only add accuracy).
+// largest term count (extra terms only add accuracy), counted by one ballot:
+// lane i holds thr_lane = kThrF32[i] (infinity from lane kEasyTerms on).
 template <int Q, int WM, bool AD>
 __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
                                            const StagedF32& tab, const QStage<Q>& st,
                                            int lane, int c0, const float (&Ev)[Q],
                                            const int (&lo)[Q], const int (&hi)[Q],
-                                           const bool (&ok)[Q], bool uni, bool (&stiff)[Q]) {
+                                           const bool (&ok)[Q], bool uni, bool (&stiff)[Q], float thr_lane) {
   int w[Q];
   float v[Q][WM];
 #pragma unroll
@@ -159,7 +162,7 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     const int base = ok[j] ? lo[j] : 0;
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r) {
-      const float4 h = tab.hi[min(base + r, ION_MAX_Z)];
+      const float4 h = tab.hi[base + r];  // < ION_MAX_Z + ION_MAX_WINDOW
       const float q = h.z * f.rE;
       const float y = (fmaf(-h.y, f.lg, h.x) - q) + h.w;
       const bool on = live && r < w[j] - 1 && q <= (float)kCutoffLog2;
@@ -177,20 +180,21 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
   // the warp's largest 2 max(W dt) (non-negative floats order like their
   // bits), then its term count once
   const float xw = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(xl)));
-  const int Rw = DDParams<float>::terms(xw, kEasyTerms);
+  const int Rw = __popc(__ballot_sync(kFull, xw > thr_lane));
   float dne[Q];
   int nlo[Q], nhi[Q];
   // u = (dt A)^k v unnormalized (|dt A| <= 2 kLamEasy keeps it small);
   // inc = sum_k u / k!.  The term loop is outermost so that the Q cells'
-  // recurrences interleave.  Stiff cells and w < 2 start from u = 0, stay at
-  // inc = 0, and are skipped below.
+  // recurrences interleave.  Slots past a cell's window start from whatever
+  // the stage holds there: their rates and the rate into them are zero, so
+  // their u is zero after one term and their inc stays zero.  Stiff cells
+  // run with rates above kLamEasy; their inc is never read.
   float u[Q][WM], inc[Q][WM];
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
-    const bool run = !stiff[j] && w[j] >= 2;
 #pragma unroll
     for (int i = 0; i < WM; ++i) {
-      u[j][i] = run && i < w[j] ? v[j][i] : 0.0f;
+      u[j][i] = v[j][i];
       inc[j][i] = 0.0f;
     }
   }
@@ -297,15 +301,25 @@ constexpr size_t stream_smem(int njobs) {
   return (size_t)njobs * sizeof(StagedF32) + (size_t)W * kStages * sizeof(QStage<Q>);
 }
 
+// Registers per thread of the streaming kernel, by cells per lane: 80 lets
+// three blocks of 8 warps (24 warps) share an SM's 64K registers with no
+// spill at Q = 2; left to itself the compiler takes about 90, and two blocks.
+template <int Q>
+constexpr int stream_regs() {
+  return Q == 1 ? 64 : Q == 2 ? 80 : 128;
+}
+
 // AD: the adaptive window policy (a separate instantiation, so that the
 // fixed rule's kernels carry none of it).
 template <int Q, int W, bool AD>
-__global__ void __launch_bounds__(W * 32)
+__global__ void __maxnreg__(stream_regs<Q>())
     ion_stream_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   StagedF32* tabs = reinterpret_cast<StagedF32*>(smem);
   QStage<Q>* ring = reinterpret_cast<QStage<Q>*>(smem + (size_t)a.njobs * sizeof(StagedF32));
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
+  for (int j = threadIdx.x >> 5; j < a.njobs; j += W)
+    stage_cold_f32(a.job[j].tab, a.pol.log2dt, &tabs[j], threadIdx.x & 31);
   {
     // plane slots past a cell's window are read (and ignored); keep them
     // finite
@@ -389,22 +403,30 @@ __global__ void __launch_bounds__(W * 32)
     cp_async_commit();
   };
 
-  // chunk k lives in stage s0, k+1 in s1, k+2 in s2
-  int s0 = 0, s1 = 1, s2 = 2;
-  issue_front(0, s0);
-  issue_front(1, s1);
-  cp_async_wait<1>();  // front(0)
+  const float thr_lane = lane < kEasyTerms ? kThrF32[lane] : __int_as_float(0x7f800000);
+  // Chunk k lives in stage k mod 4.  Commit groups go out in the order
+  // front(k+3), planes(k+2) in iteration k, so one wait that leaves the two
+  // newest pending (planes(k+1), front(k+3)) completes front(k+2) and
+  // planes(k): the planes arrive two iterations after they are requested,
+  // which hides the memory latency behind chunks that take little
+  // arithmetic.
+  static_assert(kStages == 4, "stage k mod 4");
+  issue_front(0, 0);
+  issue_front(1, 1);
+  issue_front(2, 2);
+  cp_async_wait<2>();  // front(0)
   __syncwarp();
-  issue_planes(0, s0);
+  issue_planes(0, 0);
+  cp_async_wait<2>();  // front(1)
+  __syncwarp();
+  issue_planes(1, 1);
   for (int k = 0; k < K; ++k) {
-    issue_front(k + 2, s2);
-    cp_async_wait<2>();  // front(k+1): pending are planes(k), front(k+2)
+    issue_front(k + 3, (k + 3) & 3);
+    cp_async_wait<2>();  // front(k+2) and planes(k)
     __syncwarp();
-    issue_planes(k + 1, s1);
-    cp_async_wait<2>();  // planes(k): pending are front(k+2), planes(k+1)
-    __syncwarp();
+    issue_planes(k + 2, (k + 2) & 3);
 
-    const QStage<Q>& st = S[s0];
+    const QStage<Q>& st = S[k & 3];
     const int g = gw + k * TW;
     const int jid = job_of(a, g);
     const JobIO& J = a.job[jid];
@@ -447,17 +469,45 @@ __global__ void __launch_bounds__(W * 32)
 #pragma unroll
     for (int j = 0; j < Q; ++j) stiff[j] = false;
     const StagedF32& tab = tabs[jid];
-    if (WMw <= 1) {
+    // Cold chunks: every cell has w < 2 or |E| below the field at which its
+    // largest window rate reaches 2^kColdLog2.  The series would take no
+    // term (2 W dt <= kThrF32[0]), so the step leaves N as it is and frees
+    // no electron: dne is written, and k_lo/k_hi where the window slides.
+    // (The adaptive policy's rules go the full way.)
+    bool cold = WMw <= 1;
+    if constexpr (!AD) {
+      if (!cold) {
+        bool c = true;
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+          c = c && (!ok[j] || hi[j] == lo[j] ||
+                    fabsf(Ev[j]) < tab.ecold[min(lo[j], ION_MAX_Z)]);
+        cold = __all_sync(kFull, c);
+      }
+    }
+    if (cold) {
       float* D = static_cast<float*>(J.dne);
 #pragma unroll
-      for (int j = 0; j < Q; ++j)
-        if (ok[j]) __stcs(D + c0 + j, 0.0f);
+      for (int j = 0; j < Q; ++j) {
+        if (!ok[j]) continue;
+        __stcs(D + c0 + j, 0.0f);
+        if (!AD && (a.pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi[j] > lo[j] &&
+            hi[j] < J.Z && vget(st.P[0][lane], j) < a.pol.eps_f) {
+          float v[ION_MAX_WINDOW];
+#pragma unroll
+          for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = vget(st.P[r][lane], j);
+          int nl = lo[j], nh = hi[j];
+          slide_window<float, ION_MAX_WINDOW>(v, hi[j] - lo[j] + 1, J.Z, a.pol.eps_f, nl, nh);
+          J.lo[c0 + j] = (uint8_t)nl;
+          J.hi[c0 + j] = (uint8_t)nh;
+        }
+      }
     } else if (WMw == 2) {
-      easy_cells<Q, 2, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+      easy_cells<Q, 2, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
     } else if (WMw <= 4) {
-      easy_cells<Q, 4, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+      easy_cells<Q, 4, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
     } else {
-      easy_cells<Q, 6, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff);
+      easy_cells<Q, 6, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
     }
     // stiff cells: their inputs (as loaded) go to the record queue
     bool any = false;
@@ -473,10 +523,6 @@ __global__ void __launch_bounds__(W * 32)
       }
     }
     __syncwarp();
-    const int t = s0;
-    s0 = s1;
-    s1 = s2;
-    s2 = t;
   }
   cp_async_wait<0>();
 
@@ -518,8 +564,8 @@ __device__ __forceinline__ bool record_cell(const BatchArgs& a, const StagedF32&
                                             const JobIO& J, int64_t i, int c, float Ec,
                                             int lo, int hi) {
   float v[W];
-#pragma unroll
   const int w = hi - lo + 1;
+#pragma unroll
   for (int r = 0; r < W; ++r)
     v[r] = r < w ? __ldcs(a.ws.rec_V + (int64_t)r * a.ws.rec_cap + i) : 0.0f;
   return finish_cell<F32Form, W>(J, a.pol, tab, c, Ec, lo, hi, v, true);

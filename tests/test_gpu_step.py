@@ -389,3 +389,67 @@ def test_cell_ranges_with_offset():
     assert torch.equal(d1, d2)
     with pytest.raises(ValueError):
         ionize.step(sp, wl.E, N2, lo2, hi2, 0.05, d2, offset=n - 10, ncells=20)
+
+
+def _field_at_rate(osp, k, log2_rate, dt=0.05):
+    """|E| at which the oracle's W_k dt equals 2^log2_rate (bisection in
+    log E; W_k increases with |E| below that point)."""
+    a, b = 1e-3, 1e7
+    for _ in range(200):
+        m = math.sqrt(a * b)
+        w = oracle.rates(osp, np.array([m]), k, k + 1)[0, 0] * dt
+        if w > 0 and math.log2(w) >= log2_rate:
+            b = m
+        else:
+            a = m
+    return a
+
+
+def test_cold_chunks():
+    """Chunks of cells whose window rates all have W dt far below the first
+    Taylor term's threshold keep N bit for bit and free no electron; a cell
+    in such a chunk whose lowest states hold less than eps_shift still
+    slides (twice where two states are below it), and a chunk with one hot
+    cell takes the full step.  All of it matches the oracle."""
+    sd = W.nitrogen()
+    osp = oracle_species(sd)
+    n = 64 * 40 + 17
+    idx = torch.arange(n)
+    lo = (W.uniform(11, 1, idx) * 5).long().clamp(max=4)
+    hi = lo + 2
+    root = [_field_at_rate(osp, k, -30.0) for k in range(7)]
+    E = torch.tensor([0.5 * root[int(k)] for k in lo], dtype=torch.float32)
+    E[idx % 3 == 0] *= 0.01
+    E[idx % 7 == 0] = 0.0
+    hot = 11 * 64 + 5
+    E[hot] = 3.0 * root[int(lo[hot])]
+    ld = (n + 3) // 4 * 4
+    N = torch.zeros((8, ld), dtype=torch.float32)
+    p = W.uniform(11, 2, idx).to(torch.float32) * 0.5 + 0.25
+    N[lo, idx] = p
+    N[lo + 1, idx] = (1 - p) * 0.75
+    N[lo + 2, idx] = 1 - p - (1 - p) * 0.75
+    slides = [3 * 64 + 9, 7 * 64 + 40]
+    for c in slides:
+        N[lo[c], c] = 1e-8
+        N[lo[c] + 1, c] = 1 - 1e-8 - N[lo[c] + 2, c]
+    c2 = 9 * 64 + 17  # two states below eps_shift: slides twice
+    lo[c2], hi[c2] = 1, 3
+    E[c2] = 0.5 * root[1]
+    N[:, c2] = 0.0
+    N[1, c2], N[2, c2], N[3, c2] = 1e-8, 2e-8, 1 - 3e-8
+    slides.append(c2)
+    out, ref = run_both(sd, E, N, lo.to(torch.uint8), hi.to(torch.uint8))
+    check(out, ref, lo.to(torch.uint8), hi.to(torch.uint8), ionize.ION_F32)
+    cold = np.ones(n, bool)
+    cold[11 * 64:12 * 64] = False
+    cold[slides] = False
+    cold[64 * 40:] = False  # the ragged tail takes the record path
+    Nin = N.numpy()
+    assert np.array_equal(out["N"][:, :n][:, cold].astype(np.float32), Nin[:, :n][:, cold])
+    assert np.all(out["dne"][cold] == 0.0)
+    assert np.array_equal(out["lo"], ref["lo"]) and np.array_equal(out["hi"], ref["hi"])
+    for c in slides[:2]:
+        assert out["lo"][c] == lo[c] + 1
+    assert out["lo"][c2] == 3 and out["hi"][c2] == 5
+    assert out["dne"][hot] > 0.0
