@@ -78,19 +78,31 @@ __device__ __forceinline__ void warp_append(uint32_t* counter, uint32_t* queue,
   }
 }
 
-// Appends the record of a stiff cell (one atomic per warp).  Every lane of
-// the warp calls this; `take` lanes pass their cell's inputs.
+// Appends the record of a stiff cell (one atomic per warp and width class).
+// Every lane of the warp calls this; `take` lanes pass their cell's inputs.
+// Records of windows of at most kRecNarrow states fill the record arrays
+// from the front, wider ones from the back, so that the stiff kernel's
+// warps see one class each and run the shorter divided-difference table
+// wherever they can.
 __device__ __forceinline__ void append_record(const Scratch& S, bool take, int job,
                                               int c, float Ec, int lo, int hi,
                                               const float* v) {
-  const unsigned m = __ballot_sync(kFull, take);
-  if (!m) return;
+  const bool wide = hi - lo + 1 > kRecNarrow;
+  const unsigned mn = __ballot_sync(kFull, take && !wide);
+  const unsigned mw = __ballot_sync(kFull, take && wide);
+  if (!(mn | mw)) return;
   const int lane = threadIdx.x & 31;
-  unsigned base = 0;
-  if (lane == 0) base = atomicAdd(&S.hdr[kHdrStiff], (unsigned)__popc(m));
-  base = __shfl_sync(kFull, base, 0);
+  unsigned bn = 0, bw = 0;
+  if (lane == 0) {
+    if (mn) bn = atomicAdd(&S.hdr[kHdrRecNarrow], (unsigned)__popc(mn));
+    if (mw) bw = atomicAdd(&S.hdr[kHdrRecWide], (unsigned)__popc(mw));
+  }
+  bn = __shfl_sync(kFull, bn, 0);
+  bw = __shfl_sync(kFull, bw, 0);
   if (take) {
-    const unsigned i = base + __popc(m & ((1u << lane) - 1u));
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned i = wide ? (unsigned)S.rec_cap - 1u - (bw + __popc(mw & below))
+                            : bn + __popc(mn & below);
     S.rec_c[i] = (uint32_t)c;
     S.rec_job[i] = (uint8_t)job;
     S.rec_E[i] = Ec;

@@ -12,11 +12,16 @@ namespace ion {
 // Workspace header (uint32 words at the start of the workspace).
 constexpr int kHdrFallback = 0;  // cells whose coefficients were done in FP64
 constexpr int kHdrInvalid = 1;   // cells skipped because their window is invalid
-constexpr int kHdrStiff = 2;     // stiff-cell records written by the streaming kernel
+constexpr int kHdrStiff = 2;     // stiff-cell records (written by the stiff kernel: 6 + 7)
 constexpr int kHdrSurrogate = 3; // surrogate step: cells whose rates came from the network
 constexpr int kHdrPlain = 4;     // surrogate step: cells that took the rates of Eq. 1
 constexpr int kHdrTimeout = 5;   // surrogate step: non-zero if a bounded wait gave up
-constexpr int kHdrWords = 6;
+constexpr int kHdrRecNarrow = 6; // records of windows of <= kRecNarrow states (from the front)
+constexpr int kHdrRecWide = 7;   // records of wider windows (from the back of the arrays)
+constexpr int kHdrWords = 8;
+// Records of at most this many window states take the short divided-difference
+// table (3 rates, 7 subsets); wider ones the long one (5 rates, 31 subsets).
+constexpr int kRecNarrow = 4;
 constexpr size_t kHdrBytes = 256;
 
 // Largest number of species one batched launch advances.

@@ -576,14 +576,23 @@ __global__ void __launch_bounds__(256)
   __shared__ StagedF32 tabs[kMaxJobs];
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   __syncthreads();
-  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrStiff]);
+  // narrow records at [0, nn), wide ones at [cap - nw, cap); thread t < nn_up
+  // takes narrow record t, t >= nn_up wide record cap - 1 - (t - nn_up)
+  // (both counts rounded up to whole warps, so each warp sees one class)
+  const unsigned nn = *((volatile unsigned*)&a.ws.hdr[kHdrRecNarrow]);
+  const unsigned nw = *((volatile unsigned*)&a.ws.hdr[kHdrRecWide]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ws.hdr[kHdrStiff] = nn + nw;
   const unsigned stride = gridDim.x * blockDim.x;
-  const unsigned n_up = (n + 31u) & ~31u;  // whole warps stay in the loop
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_up; i += stride) {
+  const unsigned nn_up = (nn + 31u) & ~31u;
+  const unsigned n_up = nn_up + ((nw + 31u) & ~31u);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n_up; t += stride) {
+    const bool wide = t >= nn_up;  // warp-uniform
+    const unsigned i = wide ? (unsigned)a.ws.rec_cap - 1u - (t - nn_up) : t;
+    const bool have = wide ? t - nn_up < nw : t < nn;
     bool fb = false;
     int c = 0, jid = 0, lo = 0, hi = -1;
     float Ec = 0.0f;
-    if (i < n) {
+    if (have) {
       c = (int)__ldcs(a.ws.rec_c + i);
       jid = a.ws.rec_job[i];
       Ec = __ldcs(a.ws.rec_E + i);
@@ -591,21 +600,25 @@ __global__ void __launch_bounds__(256)
       lo = lh & 0xff;
       hi = lh >> 8;
     }
-    // the warp's widest window picks one of three width bounds for all its
-    // lanes (fewer code paths, no divergence by width)
+    // the warp's widest window picks the width bound for all its lanes
+    // (fewer code paths, no divergence by width)
     const int wl = hi - lo + 1;
     const int Wm = __reduce_max_sync(kFull, wl);
     if (wl >= 1) {
       const JobIO& J = a.job[jid];
       const StagedF32& tab = tabs[jid];
-      if (wl == 1)
-        fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi);
-      else if (Wm <= 2)
-        fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi);
-      else if (Wm <= 4)
-        fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi);
-      else
+      // (a bound of 5 for warps of 5-state windows measured slower: the
+      // extra instantiation costs more than its shorter table saves)
+      static_assert(kRecNarrow == 4, "width bounds of the two record classes");
+      if (wide) {
         fb = record_cell<6>(a, tab, J, i, c, Ec, lo, hi);
+      } else if (wl == 1) {
+        fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi);
+      } else if (Wm <= 2) {
+        fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi);
+      } else {
+        fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi);
+      }
     }
     warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb, (uint32_t)c,
                 (uint8_t)jid);
