@@ -18,7 +18,8 @@ constexpr int kHdrPlain = 4;     // surrogate step: cells that took the rates of
 constexpr int kHdrTimeout = 5;   // surrogate step: non-zero if a bounded wait gave up
 constexpr int kHdrRecNarrow = 6; // records of windows of <= kRecNarrow states (from the front)
 constexpr int kHdrRecWide = 7;   // records of wider windows (from the back of the arrays)
-constexpr int kHdrWords = 8;
+constexpr int kHdrChunk = 8;     // streaming kernel: next chunk to hand out
+constexpr int kHdrWords = 9;
 // Records of at most this many window states take the short divided-difference
 // table (3 rates, 7 subsets); wider ones the long one (5 rates, 31 subsets).
 constexpr int kRecNarrow = 4;

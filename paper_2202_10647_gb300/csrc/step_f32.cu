@@ -98,7 +98,11 @@ struct QStage {
   uint32_t lo[8 * Q];           // k_lo of the chunk's 32*Q cells
   uint32_t hi[8 * Q];           // k_hi
   V P[ION_MAX_WINDOW][32];      // P[r][lane] component j = N[lo_j + r] of cell j
+  int g;                        // the chunk (>= nchunks: none)
 };
+
+// Chunks are handed out in runs of this many consecutive ones.
+constexpr int kRun = 4;
 
 // The Q bytes of a lane in a packed byte array, and whether they are equal.
 template <int Q>
@@ -335,13 +339,31 @@ __global__ void __maxnreg__(stream_regs<Q>())
   QStage<Q>* S = ring + wib * kStages;
   const int gw = blockIdx.x * W + wib;
   const int TW = gridDim.x * W;
-  const int K = gw < a.nchunks ? (a.nchunks - 1 - gw) / TW + 1 : 0;
   using V = typename VecOf<Q>::T;
 
-  // |E|, k_lo, k_hi of chunk k into stage sg (one commit group)
-  auto issue_front = [&](int k, int sg) {
-    if (k < K) {
-      const int g = gw + k * TW;
+  // Each warp draws its chunks in runs of kRun consecutive ones from a
+  // counter in the workspace header, so that warps whose chunks are cheap
+  // (cold) take more of them and all warps run out of work together.
+  uint32_t* const next = &a.ws.hdr[kHdrChunk];
+  int gnext = 0;
+  if (lane == 0) gnext = (int)atomicAdd(next, (unsigned)kRun);
+  gnext = __shfl_sync(kFull, gnext, 0);
+  auto take_chunk = [&]() -> int {
+    const int g = gnext;
+    if (g >= a.nchunks) return g;
+    if (++gnext % kRun == 0) {
+      int b = 0;
+      if (lane == 0) b = (int)atomicAdd(next, (unsigned)kRun);
+      gnext = __shfl_sync(kFull, b, 0);
+    }
+    return g;
+  };
+
+  // |E|, k_lo, k_hi of the next chunk into stage sg (one commit group)
+  auto issue_front = [&](int sg) {
+    const int g = take_chunk();
+    if (lane == 0) S[sg].g = g;
+    if (g < a.nchunks) {
       const JobIO& J = a.job[job_of(a, g)];
       const int cb = (g - J.chunk0) * kChunk;
       QStage<Q>& st = S[sg];
@@ -366,10 +388,10 @@ __global__ void __maxnreg__(stream_regs<Q>())
     }
     cp_async_commit();
   };
-  // the window planes of the lane's cells of chunk k in stage sg
-  auto issue_planes = [&](int k, int sg) {
-    if (k < K) {
-      const int g = gw + k * TW;
+  // the window planes of the lane's cells of the chunk in stage sg
+  auto issue_planes = [&](int sg) {
+    const int g = S[sg].g;
+    if (g < a.nchunks) {
       const JobIO& J = a.job[job_of(a, g)];
       const int c0 = (g - J.chunk0) * kChunk + Q * lane;
       QStage<Q>& st = S[sg];
@@ -411,23 +433,24 @@ __global__ void __maxnreg__(stream_regs<Q>())
   // which hides the memory latency behind chunks that take little
   // arithmetic.
   static_assert(kStages == 4, "stage k mod 4");
-  issue_front(0, 0);
-  issue_front(1, 1);
-  issue_front(2, 2);
+  issue_front(0);
+  issue_front(1);
+  issue_front(2);
   cp_async_wait<2>();  // front(0)
   __syncwarp();
-  issue_planes(0, 0);
+  issue_planes(0);
   cp_async_wait<2>();  // front(1)
   __syncwarp();
-  issue_planes(1, 1);
-  for (int k = 0; k < K; ++k) {
-    issue_front(k + 3, (k + 3) & 3);
+  issue_planes(1);
+  for (int k = 0;; ++k) {
+    issue_front((k + 3) & 3);
     cp_async_wait<2>();  // front(k+2) and planes(k)
     __syncwarp();
-    issue_planes(k + 2, (k + 2) & 3);
+    issue_planes((k + 2) & 3);
 
     const QStage<Q>& st = S[k & 3];
-    const int g = gw + k * TW;
+    const int g = st.g;
+    if (g >= a.nchunks) break;  // chunks come in increasing order: no more
     const int jid = job_of(a, g);
     const JobIO& J = a.job[jid];
     const int c0 = (g - J.chunk0) * kChunk + Q * lane;
