@@ -429,6 +429,38 @@ __device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
   }
 }
 
+// The same for nodes in non-decreasing order, z[0] <= ... <= z[NR-1], and
+// only the contiguous ranges [j, i] that dd_update reads: a range's
+// smallest and largest nodes are its ends, so dd_exp_all's recurrence
+// removes its first or its last node and stays on contiguous ranges
+// (NR(NR-1)/2 of them instead of 2^NR - NR - 1 subsets), dividing by the
+// same spread z[i] - z[j].
+template <typename T, int NR>
+__device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR],
+                                              T (&D)[1 << NR]) {
+  using P = DDParams<T>;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) D[1 << i] = ez[i];
+#pragma unroll
+  for (int len = 2; len <= NR; ++len) {
+#pragma unroll
+    for (int j = 0; j + len <= NR; ++j) {
+      const int i = j + len - 1;
+      const T s = z[i] - z[j];
+      T d;
+      if (s >= P::tau) {
+        d = P::div(D[range_mask(j + 1, i)] - D[range_mask(j, i - 1)], s);
+      } else {
+        d = ez[i] * dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
+                                 NR > 2 ? z[NR > 2 ? 2 : 0] : T(0),
+                                 NR > 3 ? z[NR > 3 ? 3 : 0] : T(0),
+                                 NR > 4 ? z[NR > 4 ? 4 : 0] : T(0), range_mask(j, i), z[i], s);
+      }
+      D[range_mask(j, i)] = d;
+    }
+  }
+}
+
 // Small rates: N' = sum_k (dt A)^k N / k! applied to the window vector
 // directly.  With every W dt <= prop_max the norm of dt A is at most
 // 2 prop_max, the terms shrink from the first, and R terms leave a remainder
@@ -493,8 +525,17 @@ __device__ __forceinline__ T dd_update(T (&v)[WM], const T (&lam)[WM], int w) {
     z[r] = -l;
     ez[r] = exp(-l);
   }
+  // Rates that fall along the window (the usual ladder: each state is
+  // harder to ionize than the one below) give non-decreasing nodes and the
+  // short table; others take every subset.
+  bool sorted = true;
+#pragma unroll
+  for (int r = 0; r + 1 < NR; ++r) sorted = sorted && z[r] <= z[r + 1];
   T D[1 << NR];
-  dd_exp_all<T, NR>(z, ez, D);
+  if (sorted)
+    dd_exp_ranges<T, NR>(z, ez, D);
+  else
+    dd_exp_all<T, NR>(z, ez, D);
   T out[NR];
 #pragma unroll
   for (int i = 0; i < NR; ++i) {

@@ -2,8 +2,9 @@
 // one persistent launch over the cells of up to kMaxJobs species, then two
 // small kernels over the cells it left behind.
 //
-//   ion_stream_kernel<Q, W>  every warp walks its own sequence of chunks of
-//       32*Q cells (Q consecutive cells per lane) through a 4-stage ring in
+//   ion_stream_kernel<Q, W>  every warp draws chunks of 32*Q cells (Q
+//       consecutive cells per lane) in runs of four from a counter in the
+//       workspace header and moves them through a 4-stage ring in
 //       shared memory.  cp.async brings |E|, k_lo and k_hi in three chunks
 //       ahead and each lane's own window planes two chunks ahead (one copy of
 //       4*Q bytes per plane when the lane's cells share their window), so the
