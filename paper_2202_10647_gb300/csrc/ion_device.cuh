@@ -429,12 +429,12 @@ __device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
   }
 }
 
-// The same for nodes in non-decreasing order, z[0] <= ... <= z[NR-1], and
-// only the contiguous ranges [j, i] that dd_update reads: a range's
-// smallest and largest nodes are its ends, so dd_exp_all's recurrence
-// removes its first or its last node and stays on contiguous ranges
-// (NR(NR-1)/2 of them instead of 2^NR - NR - 1 subsets), dividing by the
-// same spread z[i] - z[j].
+// The same for nodes in monotone order (z[0] <= ... <= z[NR-1] or the
+// reverse), and only the contiguous ranges [j, i] that dd_update reads: a
+// range's smallest and largest nodes are its ends, so dd_exp_all's
+// recurrence removes its first or its last node and stays on contiguous
+// ranges (NR(NR-1)/2 of them instead of 2^NR - NR - 1 subsets), dividing
+// by the same spread |z[i] - z[j]|.
 template <typename T, int NR>
 __device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR],
                                               T (&D)[1 << NR]) {
@@ -446,15 +446,18 @@ __device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR
 #pragma unroll
     for (int j = 0; j + len <= NR; ++j) {
       const int i = j + len - 1;
-      const T s = z[i] - z[j];
+      const T dz = z[i] - z[j];
+      const T s = fabs(dz);
       T d;
       if (s >= P::tau) {
-        d = P::div(D[range_mask(j + 1, i)] - D[range_mask(j, i - 1)], s);
+        d = P::div(D[range_mask(j + 1, i)] - D[range_mask(j, i - 1)], dz);
       } else {
-        d = ez[i] * dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
-                                 NR > 2 ? z[NR > 2 ? 2 : 0] : T(0),
-                                 NR > 3 ? z[NR > 3 ? 3 : 0] : T(0),
-                                 NR > 4 ? z[NR > 4 ? 4 : 0] : T(0), range_mask(j, i), z[i], s);
+        const bool up = dz >= T(0);  // the largest node is the range's last
+        d = (up ? ez[i] : ez[j]) *
+            dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
+                         NR > 2 ? z[NR > 2 ? 2 : 0] : T(0), NR > 3 ? z[NR > 3 ? 3 : 0] : T(0),
+                         NR > 4 ? z[NR > 4 ? 4 : 0] : T(0), range_mask(j, i), up ? z[i] : z[j],
+                         s);
       }
       D[range_mask(j, i)] = d;
     }
@@ -525,12 +528,17 @@ __device__ __forceinline__ T dd_update(T (&v)[WM], const T (&lam)[WM], int w) {
     z[r] = -l;
     ez[r] = exp(-l);
   }
-  // Rates that fall along the window (the usual ladder: each state is
-  // harder to ionize than the one below) give non-decreasing nodes and the
-  // short table; others take every subset.
-  bool sorted = true;
+  // Rates that fall along the window (the usual ladder near threshold: each
+  // state harder to ionize than the one below) or rise along it (far above
+  // the barrier, where Eq. 1 grows with the charge) give monotone nodes and
+  // the short table; others take every subset.
+  bool up = true, down = true;
 #pragma unroll
-  for (int r = 0; r + 1 < NR; ++r) sorted = sorted && z[r] <= z[r + 1];
+  for (int r = 0; r + 1 < NR; ++r) {
+    up = up && z[r] <= z[r + 1];
+    down = down && z[r] >= z[r + 1];
+  }
+  const bool sorted = up || down;
   T D[1 << NR];
   if (sorted)
     dd_exp_ranges<T, NR>(z, ez, D);

@@ -849,8 +849,27 @@ cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms
   return launch_fb_f32(a, num_sms, s);
 }
 
+// The record kernel's grid is one wave of resident blocks: a second, partial
+// wave would start its share of the records only after the first finished.
+int g_stiff_fit[kMaxDevices] = {};
+
 cudaError_t launch_stiff_f32(const BatchArgs& a, int num_sms, cudaStream_t s) {
-  ion_stiff_kernel<<<4 * num_sms, 256, 0, s>>>(a);
+  int dev = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cache = dev >= 0 && dev < kMaxDevices;
+  {
+    std::lock_guard<std::mutex> lock(g_fit_mu);
+    if (cache) fit = g_stiff_fit[dev];
+    if (fit < 1) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, ion_stiff_kernel, 256, 0)) !=
+          cudaSuccess)
+        return e;
+      fit = fit < 1 ? 1 : fit;
+      if (cache) g_stiff_fit[dev] = fit;
+    }
+  }
+  ion_stiff_kernel<<<fit * num_sms, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

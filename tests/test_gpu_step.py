@@ -453,3 +453,40 @@ def test_cold_chunks():
         assert out["lo"][c] == lo[c] + 1
     assert out["lo"][c2] == 3 and out["hi"][c2] == 5
     assert out["dne"][hot] > 0.0
+
+
+@pytest.mark.parametrize("flags", [ionize.ION_F32, ionize.ION_F64_PLAIN])
+def test_stiff_windows_rate_order(flags):
+    """Stiff windows (some W dt > 1) of every width whose rates fall or rise
+    along the window (the contiguous-range divided differences) and whose
+    rates do neither (a ladder with potentials that go down and up again:
+    every subset of the rates), both against the oracle; each record class
+    of the FP32 path (windows of up to 4 states, and wider) is filled."""
+    rising = W.SpeciesData("rising", [12.0, 18.0, 26.0, 35.0, 47.0, 60.0, 75.0],
+                           [1, 1, 1, 1, 1, 0, 0], [0] * 7)
+    zigzag = W.SpeciesData("zigzag", [20.0, 14.0, 30.0, 22.0, 40.0, 31.0, 55.0],
+                           [1, 0, 1, 0, 1, 0, 1], [0] * 7)
+    for sd in (rising, zigzag):
+        n = 64 * 24 + 11
+        idx = torch.arange(n)
+        w = 2 + (idx % 5)                       # widths 2..6
+        lo = (W.uniform(21, 1, idx) * (8 - w).double()).long()
+        hi = lo + w - 1
+        # fields from well below to far above the windows' first thresholds
+        E = (10.0 ** (1.5 + 2.0 * W.uniform(21, 2, idx))).to(torch.float32)
+        ld = (n + 3) // 4 * 4
+        N = torch.zeros((8, ld), dtype=torch.float32)
+        p = W.uniform(21, 3, idx).to(torch.float32)
+        for r in range(6):
+            on = (r < w - 1)
+            share = (p * (r + 1)) % 1.0 + 0.05
+            N[(lo + r).clamp(max=7)[on], idx[on]] = share[on]
+        tot = N[:, :n].sum(0)
+        N[:, :n] /= tot
+        lo8, hi8 = lo.to(torch.uint8), hi.to(torch.uint8)
+        out, ref = run_both(sd, E, N, lo8, hi8, flags=flags)
+        check(out, ref, lo8, hi8, flags)
+        osp = oracle_species(sd)
+        Wr = oracle.rates(osp, E.double().numpy(), 0, 7) * 0.05
+        stiff = np.array([Wr[int(lo[c]):int(hi[c]), c].max() > 1.0 for c in range(n)])
+        assert stiff[(w <= 4).numpy()].sum() > 50 and stiff[(w > 4).numpy()].sum() > 50
