@@ -118,19 +118,21 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // W dt below 2^kColdLog2 (9.3e-10) is far under the 1.5e-9 at which the FP32
-// Taylor series takes its first term (2 W dt > kThrF32[0]).
+// Taylor series takes its first term (2 W dt > kThrF32[0]); below
+// 2^kColdLog2F64 (3.5e-18) likewise for the FP64 series (kThrF64[0] = 2e-17).
 constexpr float kColdLog2 = -30.0f;
+constexpr float kColdLog2F64 = -58.0f;
 
 // Field strength E_c below which y(E) = a - b log2 E - C/E, the log2 of W dt
-// (Eq. 1), lies under kColdLog2; 0 when no such bound is found safely.  With
-// u = log2 E, g(u) = y - kColdLog2 is concave in u (g'' = -C ln^2 2 2^-u), so
+// (Eq. 1), lies under tlog2; 0 when no such bound is found safely.  With
+// u = log2 E, g(u) = y - tlog2 is concave in u (g'' = -C ln^2 2 2^-u), so
 // Newton's iterates that start where g' > 0 approach the root from below
 // after their first step.  E_c is the last iterate less 2^-8 relative:
 // g(log2 E_c) <= about -0.25, margin for the FP32 arithmetic here and for
-// the FP32 rate evaluation that E_c stands in for.  Below the root g
-// increases with u, so every E < E_c has y < kColdLog2 as well.
-__device__ __forceinline__ float cold_field(double a_d, double b_d, double C_d) {
-  const float am = (float)a_d - kColdLog2, b = (float)b_d, C = (float)C_d;
+// the rate evaluation that E_c stands in for.  Below the root g increases
+// with u, so every E < E_c has y < tlog2 as well.
+__device__ __forceinline__ float cold_field(double a_d, double b_d, double C_d, float tlog2) {
+  const float am = (float)a_d - tlog2, b = (float)b_d, C = (float)C_d;
   constexpr float kLn2 = 0.693147181f;
   // the start u0 = log2(C / am) has g'(u0) = am ln 2 - b; demand a margin
   if (!(C > 0.0f) || !(am * kLn2 > b + 1.0f) || !(am < 1e30f)) return 0.0f;
@@ -146,19 +148,19 @@ __device__ __forceinline__ float cold_field(double a_d, double b_d, double C_d) 
   return ex2_approx(u) * (1.0f - 1.0f / 256.0f);
 }
 
-// One warp: ecold of one species (threads k < Z of the table in two rounds
-// of 32), each state's own cold field turned into the minimum over the
-// states at or above it by a suffix scan; the padding past Z holds 0 (never
-// cold).
-__device__ __forceinline__ void stage_cold_f32(const SpeciesTable* t, double log2dt,
-                                               StagedF32* s, int lane) {
+// One warp: ecold[0 .. ION_MAX_Z + ION_MAX_WINDOW) of one species for the
+// target 2^tlog2 (threads k < Z of the table in two rounds of 32), each
+// state's own cold field turned into the minimum over the states at or
+// above it by a suffix scan; the padding past Z holds 0 (never cold).
+__device__ __forceinline__ void stage_cold(const SpeciesTable* t, double log2dt, float tlog2,
+                                           float* ecold, int lane) {
   const int Z = t->Z;
   const float kInf = __int_as_float(0x7f800000);
   float m[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int k = lane + 32 * h;
-    m[h] = k < Z ? cold_field(t->a2[k] + log2dt, t->b[k], t->C[k]) : kInf;
+    m[h] = k < Z ? cold_field(t->a2[k] + log2dt, t->b[k], t->C[k], tlog2) : kInf;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const float x = __shfl_down_sync(0xffffffffu, m[h], o);
@@ -169,9 +171,9 @@ __device__ __forceinline__ void stage_cold_f32(const SpeciesTable* t, double log
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int k = lane + 32 * h;
-    s->ecold[k] = k < Z ? m[h] : 0.0f;
+    ecold[k] = k < Z ? m[h] : 0.0f;
   }
-  if (lane + 64 < ION_MAX_Z + ION_MAX_WINDOW) s->ecold[lane + 64] = 0.0f;
+  if (lane + 64 < ION_MAX_Z + ION_MAX_WINDOW) ecold[lane + 64] = 0.0f;
 }
 
 

@@ -324,7 +324,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
   QStage<Q>* ring = reinterpret_cast<QStage<Q>*>(smem + (size_t)a.njobs * sizeof(StagedF32));
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   for (int j = threadIdx.x >> 5; j < a.njobs; j += W)
-    stage_cold_f32(a.job[j].tab, a.pol.log2dt, &tabs[j], threadIdx.x & 31);
+    stage_cold(a.job[j].tab, a.pol.log2dt, kColdLog2, tabs[j].ecold, threadIdx.x & 31);
   {
     // plane slots past a cell's window are read (and ignored); keep them
     // finite

@@ -16,7 +16,9 @@ __global__ void __launch_bounds__(kThreads)
     ion_step_f64_kernel(const __grid_constant__ JobIO J,
                         const __grid_constant__ Policy pol, uint32_t* hdr) {
   __shared__ StagedF64 tab;
+  __shared__ float ecold[ION_MAX_Z + ION_MAX_WINDOW];
   stage_f64(J.tab, pol.log2dt, &tab);
+  if (threadIdx.x < 32) stage_cold(J.tab, pol.log2dt, kColdLog2F64, ecold, threadIdx.x);
   __syncthreads();
   const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cl >= J.ncells) return;
@@ -25,6 +27,26 @@ __global__ void __launch_bounds__(kThreads)
   const int lo = J.lo[c], hi = J.hi[c];
   if (!window_ok(lo, hi, J.Z)) {
     atomicAdd(&hdr[kHdrInvalid], 1u);
+    return;
+  }
+  // Cold cell (|E| below the field at which its largest window rate reaches
+  // 2^kColdLog2F64): the series would take no term (2 W dt <= kThrF64[0]),
+  // so N stays as it is and no electron is freed; only the window rule runs.
+  // (The adaptive policy goes the full way.)
+  if (!pol.adaptive && hi > lo && fabs(Ec) < (double)ecold[lo]) {
+    static_cast<double*>(J.dne)[c] = 0.0;
+    if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi < J.Z) {
+      const double* p = static_cast<const double*>(J.N) + (int64_t)lo * J.ld + c;
+      if (p[0] < pol.eps) {
+        double v[ION_MAX_WINDOW];
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = r < hi - lo ? p[(int64_t)r * J.ld] : 0.0;
+        int nl = lo, nh = hi;
+        slide_window<double, ION_MAX_WINDOW>(v, hi - lo + 1, J.Z, pol.eps, nl, nh);
+        J.lo[c] = (uint8_t)nl;
+        J.hi[c] = (uint8_t)nh;
+      }
+    }
     return;
   }
   global_cell_any<F64Form>(J, pol, tab, c, Ec, lo, hi, false);
