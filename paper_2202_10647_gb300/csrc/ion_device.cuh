@@ -219,6 +219,24 @@ __device__ __forceinline__ float rate_dt_f32(const StagedF32& t, int k,
   return ex2_approx(y);
 }
 
+// The float-float branch of rate_dt_f32 alone, for a rate its plain FP32
+// evaluation already found live and above 2^-12 (non-zero field, C/|E|
+// under the cutoff): the same value, without re-testing those.
+__device__ __forceinline__ float rate_ff_f32(const StagedF32& t, int k, const FieldF32& f) {
+  const float4 h = t.hi[k];  // a_hi, b_hi, C_hi, a_lo
+  const float2 l = t.lo[k];  // b_lo, C_lo
+  const float q = h.z * f.rE;
+  const float ql = (fmaf(-q, f.E, h.z) + l.y) * f.rE;  // C/E = q + ql
+  const float p = h.y * f.ex;
+  const float pe = fmaf(h.y, f.ex, -p);  // b_hi*ex = p + pe exactly
+  float s1, e1, s2, e2;
+  two_sum(h.x, -p, s1, e1);
+  two_sum(s1, -q, s2, e2);
+  const float small = ((h.w - pe) - ql) - fmaf(h.y, f.lm, l.x * f.lg);
+  const float tail = (e1 + e2) + small;
+  return ex2_approx(fminf(s2 + tail, 99.0f));
+}
+
 // The field's part of the FP64 exponent, once per cell: log2|E| and 1/|E|.
 struct FieldF64 {
   double lg, rE;

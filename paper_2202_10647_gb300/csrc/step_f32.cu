@@ -175,7 +175,7 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     }
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r)
-      if (lam[j][r] > kLamPrecise) lam[j][r] = rate_dt_f32(tab, base + r, f);
+      if (lam[j][r] > kLamPrecise) lam[j][r] = rate_ff_f32(tab, base + r, f);
     float lmax = 0.0f;
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
