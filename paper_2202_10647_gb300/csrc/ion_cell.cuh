@@ -212,26 +212,4 @@ __device__ __forceinline__ bool global_cell(const JobIO& J, const Policy& pol,
   return finish_cell<F, W>(J, pol, tab, c, Ec, lo, hi, v, allow_fb);
 }
 
-// Dispatch on a width known to be 1..6 (per-lane switch).
-template <class F>
-__device__ __forceinline__ bool global_cell_any(const JobIO& J, const Policy& pol,
-                                                const typename F::Staged& tab, int c,
-                                                typename F::T Ec, int lo, int hi,
-                                                bool allow_fb) {
-  switch (hi - lo + 1) {
-    case 1:
-      return global_cell<F, 1>(J, pol, tab, c, Ec, lo, hi, allow_fb);
-    case 2:
-      return global_cell<F, 2>(J, pol, tab, c, Ec, lo, hi, allow_fb);
-    case 3:
-      return global_cell<F, 3>(J, pol, tab, c, Ec, lo, hi, allow_fb);
-    case 4:
-      return global_cell<F, 4>(J, pol, tab, c, Ec, lo, hi, allow_fb);
-    case 5:
-      return global_cell<F, 5>(J, pol, tab, c, Ec, lo, hi, allow_fb);
-    default:
-      return global_cell<F, 6>(J, pol, tab, c, Ec, lo, hi, allow_fb);
-  }
-}
-
 }  // namespace ion

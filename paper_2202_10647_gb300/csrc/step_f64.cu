@@ -1,6 +1,7 @@
 // step_f64.cu -- the plain FP64 form of ion_step (ION_F64_PLAIN): FP64 data
-// and arithmetic everywhere, one cell per thread, every width and path
-// inline.  It is bound by GB300's FP64 rate, not by memory.
+// and arithmetic everywhere, one cell per thread, every path inline, the
+// warp's widest window as the width bound of all its lanes.  It is bound by
+// GB300's FP64 rate, not by memory.
 #include <cstdint>
 
 #include "ion_cell.cuh"
@@ -21,35 +22,50 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x < 32) stage_cold(J.tab, pol.log2dt, kColdLog2F64, ecold, threadIdx.x);
   __syncthreads();
   const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cl >= J.ncells) return;
-  const int c = (int)cl;
-  const double Ec = static_cast<const double*>(J.E)[c];
-  const int lo = J.lo[c], hi = J.hi[c];
-  if (!window_ok(lo, hi, J.Z)) {
-    atomicAdd(&hdr[kHdrInvalid], 1u);
-    return;
-  }
-  // Cold cell (|E| below the field at which its largest window rate reaches
-  // 2^kColdLog2F64): the series would take no term (2 W dt <= kThrF64[0]),
-  // so N stays as it is and no electron is freed; only the window rule runs.
-  // (The adaptive policy goes the full way.)
-  if (!pol.adaptive && hi > lo && fabs(Ec) < (double)ecold[lo]) {
-    static_cast<double*>(J.dne)[c] = 0.0;
-    if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi < J.Z) {
-      const double* p = static_cast<const double*>(J.N) + (int64_t)lo * J.ld + c;
-      if (p[0] < pol.eps) {
-        double v[ION_MAX_WINDOW];
+  bool act = cl < J.ncells;
+  int c = 0, lo = 0, hi = 0;
+  double Ec = 0.0;
+  if (act) {
+    c = (int)cl;
+    Ec = static_cast<const double*>(J.E)[c];
+    lo = J.lo[c];
+    hi = J.hi[c];
+    if (!window_ok(lo, hi, J.Z)) {
+      atomicAdd(&hdr[kHdrInvalid], 1u);
+      act = false;
+    } else if (!pol.adaptive && hi > lo && fabs(Ec) < (double)ecold[lo]) {
+      // Cold cell (|E| below the field at which its largest window rate
+      // reaches 2^kColdLog2F64): the series would take no term
+      // (2 W dt <= kThrF64[0]), so N stays as it is and no electron is
+      // freed; only the window rule runs.  (The adaptive policy goes the
+      // full way.)
+      act = false;
+      static_cast<double*>(J.dne)[c] = 0.0;
+      if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi < J.Z) {
+        const double* p = static_cast<const double*>(J.N) + (int64_t)lo * J.ld + c;
+        if (p[0] < pol.eps) {
+          double v[ION_MAX_WINDOW];
 #pragma unroll
-        for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = r < hi - lo ? p[(int64_t)r * J.ld] : 0.0;
-        int nl = lo, nh = hi;
-        slide_window<double, ION_MAX_WINDOW>(v, hi - lo + 1, J.Z, pol.eps, nl, nh);
-        J.lo[c] = (uint8_t)nl;
-        J.hi[c] = (uint8_t)nh;
+          for (int r = 0; r < ION_MAX_WINDOW; ++r)
+            v[r] = r < hi - lo ? p[(int64_t)r * J.ld] : 0.0;
+          int nl = lo, nh = hi;
+          slide_window<double, ION_MAX_WINDOW>(v, hi - lo + 1, J.Z, pol.eps, nl, nh);
+          J.lo[c] = (uint8_t)nl;
+          J.hi[c] = (uint8_t)nh;
+        }
       }
     }
-    return;
   }
-  global_cell_any<F64Form>(J, pol, tab, c, Ec, lo, hi, false);
+  // the warp's widest window among the cells left picks one width bound for
+  // all its lanes (a per-lane switch would run every width present)
+  const int Wm = __reduce_max_sync(0xffffffffu, act ? hi - lo + 1 : 0);
+  if (!act) return;
+  if (Wm <= 2)
+    global_cell<F64Form, 2>(J, pol, tab, c, Ec, lo, hi, false);
+  else if (Wm <= 4)
+    global_cell<F64Form, 4>(J, pol, tab, c, Ec, lo, hi, false);
+  else
+    global_cell<F64Form, 6>(J, pol, tab, c, Ec, lo, hi, false);
 }
 
 }  // namespace
