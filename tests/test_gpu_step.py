@@ -490,3 +490,45 @@ def test_stiff_windows_rate_order(flags):
         Wr = oracle.rates(osp, E.double().numpy(), 0, 7) * 0.05
         stiff = np.array([Wr[int(lo[c]):int(hi[c]), c].max() > 1.0 for c in range(n)])
         assert stiff[(w <= 4).numpy()].sum() > 50 and stiff[(w > 4).numpy()].sum() > 50
+
+
+def test_cold_cells_fp64():
+    """The FP64 form's cold cells (every window rate below W dt = 2^-58):
+    N is kept bit for bit, no electron is freed, windows whose lowest states
+    hold less than eps_shift slide (once or twice), and hot cells in the same
+    warps take the full step; all against the oracle."""
+    sd = W.nitrogen()
+    osp = oracle_species(sd)
+    n = 32 * 30 + 7
+    idx = torch.arange(n)
+    lo = (W.uniform(12, 1, idx) * 5).long().clamp(max=4)
+    hi = lo + 2
+    root = [_field_at_rate(osp, k, -58.0) for k in range(7)]
+    E = torch.tensor([0.5 * root[int(k)] for k in lo], dtype=torch.float32)
+    E[idx % 5 == 0] = 0.0
+    hot = idx % 32 == 7
+    E[hot] = torch.tensor([3.0 * root[int(k)] for k in lo[hot]], dtype=torch.float32)
+    ld = (n + 3) // 4 * 4
+    N = torch.zeros((8, ld), dtype=torch.float32)
+    p = W.uniform(12, 2, idx).to(torch.float32) * 0.5 + 0.25
+    N[lo, idx] = p
+    N[lo + 1, idx] = (1 - p) * 0.75
+    N[lo + 2, idx] = 1 - p - (1 - p) * 0.75
+    one, two = 3 * 32 + 9, 11 * 32 + 20
+    N[lo[one], one] = 1e-8
+    N[lo[one] + 1, one] = 1 - 1e-8 - N[lo[one] + 2, one]
+    lo[two], hi[two] = 1, 3
+    E[two] = 0.5 * root[1]
+    N[:, two] = 0.0
+    N[1, two], N[2, two], N[3, two] = 1e-8, 2e-8, 1 - 3e-8
+    lo8, hi8 = lo.to(torch.uint8), hi.to(torch.uint8)
+    out, ref = run_both(sd, E, N, lo8, hi8, flags=ionize.ION_F64_PLAIN)
+    check(out, ref, lo8, hi8, ionize.ION_F64_PLAIN)
+    cold = ~hot.numpy()
+    Nin = N.double().numpy()[:, :n]
+    assert np.array_equal(out["N"][:, :n][:, cold], Nin[:, cold])
+    assert np.all(out["dne"][cold] == 0.0)
+    assert np.all(out["dne"][hot.numpy()] > 0.0)
+    assert out["lo"][one] == lo[one] + 1
+    assert out["lo"][two] == 3 and out["hi"][two] == 5
+    assert np.array_equal(out["lo"], ref["lo"]) and np.array_equal(out["hi"], ref["hi"])
