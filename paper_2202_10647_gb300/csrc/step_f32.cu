@@ -404,10 +404,9 @@ __global__ void __maxnreg__(stream_regs<Q>())
         const int w = window_ok(lo0, hi0, J.Z) ? hi0 - lo0 + 1 : 0;
         const float* p = N + (int64_t)lo0 * J.ld + c0;
         V* d = &st.P[0][lane];
-        for (int r = 0; r < w; ++r) {
-          cp_async<4 * Q>(d, p);
-          p += J.ld;
-          d += 32;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+          if (r < w) cp_async<4 * Q>(d + 32 * r, p + (int64_t)r * J.ld);
         }
       } else {
         float* P0 = reinterpret_cast<float*>(&st.P[0][lane]);
@@ -598,8 +597,6 @@ __device__ __forceinline__ bool record_cell(const BatchArgs& a, const StagedF32&
 __global__ void __launch_bounds__(256)
     ion_stiff_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ StagedF32 tabs[kMaxJobs];
-  for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
-  __syncthreads();
   // narrow records at [0, nn), wide ones at [cap - nw, cap); thread t < nn_up
   // takes narrow record t, t >= nn_up wide record cap - 1 - (t - nn_up)
   // (both counts rounded up to whole warps, so each warp sees one class)
@@ -609,6 +606,9 @@ __global__ void __launch_bounds__(256)
   const unsigned stride = gridDim.x * blockDim.x;
   const unsigned nn_up = (nn + 31u) & ~31u;
   const unsigned n_up = nn_up + ((nw + 31u) & ~31u);
+  if (blockIdx.x * blockDim.x >= n_up) return;  // no record for this block
+  for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
+  __syncthreads();
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n_up; t += stride) {
     const bool wide = t >= nn_up;  // warp-uniform
     const unsigned i = wide ? (unsigned)a.ws.rec_cap - 1u - (t - nn_up) : t;
@@ -681,9 +681,10 @@ __device__ __forceinline__ void fb_cell(const JobIO& J, const Policy& pol,
 
 __global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ StagedF32 tabs[kMaxJobs];
+  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrFallback]);
+  if (blockIdx.x * blockDim.x >= n) return;  // no queued cell for this block
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   __syncthreads();
-  const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrFallback]);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += gridDim.x * blockDim.x) {
     const int c = (int)a.ws.queue[i];
