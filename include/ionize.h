@@ -306,7 +306,7 @@ ION_API int ion_conservation(const void* N, int64_t ld, int64_t ncells, int npla
 /* ---- rate surrogate: network and training --------------------------------
  * A small network maps the field magnitude to the logarithms of all Z rates
  * of a species at once (the paper evaluates Eq. 1 directly; the surrogate is
- * the learned alternative and is judged against it):
+ * the learned alternative and is measured against it):
  *   h1 = g(W1 x + b1), h2 = g(W2 h1 + b2), y = W3 h2 + b3,
  * ION_MLP_HIDDEN = 64 hidden units, K <= ION_MAX_Z outputs, g the GELU in
  * its tanh form g(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
