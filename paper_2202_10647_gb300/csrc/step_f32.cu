@@ -104,13 +104,15 @@ struct QStage {
 
 // Chunks are handed out in runs of this many consecutive ones.
 constexpr int kRun = 4;
+static_assert((kRun & (kRun - 1)) == 0, "kRun is a power of two");
 
-// The Q bytes of a lane in a packed byte array, and whether they are equal.
+// The Q bytes of a lane in a packed byte array (one load of Q bytes), and
+// whether they are equal.
 template <int Q>
 __device__ __forceinline__ uint32_t lane_bytes(const uint32_t* arr, int lane) {
   if constexpr (Q == 4) return arr[lane];
-  if constexpr (Q == 2) return (arr[lane >> 1] >> (16 * (lane & 1))) & 0xffffu;
-  return (arr[lane >> 2] >> (8 * (lane & 3))) & 0xffu;
+  if constexpr (Q == 2) return reinterpret_cast<const uint16_t*>(arr)[lane];
+  return reinterpret_cast<const uint8_t*>(arr)[lane];
 }
 template <int Q>
 __device__ __forceinline__ bool bytes_equal(uint32_t x) {
@@ -352,7 +354,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
   auto take_chunk = [&]() -> int {
     const int g = gnext;
     if (g >= a.nchunks) return g;
-    if (++gnext % kRun == 0) {
+    if ((++gnext & (kRun - 1)) == 0) {  // kRun is a power of two
       int b = 0;
       if (lane == 0) b = (int)atomicAdd(next, (unsigned)kRun);
       gnext = __shfl_sync(kFull, b, 0);
@@ -510,10 +512,16 @@ __global__ void __maxnreg__(stream_regs<Q>())
     }
     if (cold) {
       float* D = static_cast<float*>(J.dne);
+      if (uni && J.vec) {
+        float z[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) z[j] = 0.0f;
+        vstore(D + c0, z);
+      }
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
         if (!ok[j]) continue;
-        __stcs(D + c0 + j, 0.0f);
+        if (!(uni && J.vec)) __stcs(D + c0 + j, 0.0f);
         if (!AD && (a.pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi[j] > lo[j] &&
             hi[j] < J.Z && vget(st.P[0][lane], j) < a.pol.eps_f) {
           float v[ION_MAX_WINDOW];
