@@ -18,28 +18,25 @@ __global__ void __launch_bounds__(kThreads)
                         const __grid_constant__ Policy pol, uint32_t* hdr) {
   __shared__ StagedF64 tab;
   __shared__ float ecold[ION_MAX_Z + ION_MAX_WINDOW];
+  __shared__ int nq;
+  __shared__ int queue[kThreads];
+  if (threadIdx.x == 0) nq = 0;
   stage_f64(J.tab, pol.log2dt, &tab);
   if (threadIdx.x < 32) stage_cold(J.tab, pol.log2dt, kColdLog2F64, ecold, threadIdx.x);
   __syncthreads();
   const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool act = cl < J.ncells;
-  int c = 0, lo = 0, hi = 0;
-  double Ec = 0.0;
-  if (act) {
-    c = (int)cl;
-    Ec = static_cast<const double*>(J.E)[c];
-    lo = J.lo[c];
-    hi = J.hi[c];
+  if (cl < J.ncells) {
+    const int c = (int)cl;
+    const double Ec = static_cast<const double*>(J.E)[c];
+    const int lo = J.lo[c], hi = J.hi[c];
     if (!window_ok(lo, hi, J.Z)) {
       atomicAdd(&hdr[kHdrInvalid], 1u);
-      act = false;
     } else if (!pol.adaptive && hi > lo && fabs(Ec) < (double)ecold[lo]) {
       // Cold cell (|E| below the field at which its largest window rate
       // reaches 2^kColdLog2F64): the series would take no term
       // (2 W dt <= kThrF64[0]), so N stays as it is and no electron is
       // freed; only the window rule runs.  (The adaptive policy goes the
       // full way.)
-      act = false;
       static_cast<double*>(J.dne)[c] = 0.0;
       if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi < J.Z) {
         const double* p = static_cast<const double*>(J.N) + (int64_t)lo * J.ld + c;
@@ -54,10 +51,24 @@ __global__ void __launch_bounds__(kThreads)
           J.hi[c] = (uint8_t)nh;
         }
       }
+    } else {
+      queue[atomicAdd(&nq, 1)] = c;
     }
   }
-  // the warp's widest window among the cells left picks one width bound for
-  // all its lanes (a per-lane switch would run every width present)
+  __syncthreads();
+  // The block's other cells, packed into its first warps so that the FP64
+  // work runs in full warps (cold and invalid cells no longer idle lanes of
+  // it); the warp's widest window picks one width bound for all its lanes
+  // (a per-lane switch would run every width present).
+  const bool act = (int)threadIdx.x < nq;
+  int c = 0, lo = 0, hi = 0;
+  double Ec = 0.0;
+  if (act) {
+    c = queue[threadIdx.x];
+    Ec = static_cast<const double*>(J.E)[c];
+    lo = J.lo[c];
+    hi = J.hi[c];
+  }
   const int Wm = __reduce_max_sync(0xffffffffu, act ? hi - lo + 1 : 0);
   if (!act) return;
   if (Wm <= 2)
