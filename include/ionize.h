@@ -260,8 +260,9 @@ ION_API int ion_autotune(const ion_batch_job* jobs, int njobs, double dt_fs,
  * of its guests, or codes that fix their memory footprint at start-up.  This
  * entry point takes the same arguments as ion_step minus the workspace, and
  * uses instead a scratch array that is a file-scope __device__ variable of
- * this library: ION_STEP_NOALLOC_SCRATCH_BYTES (about 9.5 MB) on every GPU
- * that loads the library, held until the process exits.  The paper has no
+ * this library: ION_STEP_NOALLOC_SCRATCH_BYTES (10,486,016 bytes, about 10.5 MB
+ * or 10 MiB) on every GPU that loads the library, held until the process
+ * exits.  The paper has no
  * counterpart of this call.
  *   - ncells <= ION_STEP_NOALLOC_MAX_CELLS (262144); larger calls return
  *     ION_EINVAL (split the cells into ranges: offset E, N, k_lo, k_hi, dne
@@ -269,6 +270,9 @@ ION_API int ion_autotune(const ion_batch_job* jobs, int njobs, double dt_fs,
  *   - It allocates nothing and frees nothing.  The first call on a device
  *     looks up the device address of the array (cudaGetSymbolAddress) with
  *     that device current; make that first call before any stream capture.
+ *     The address is kept for the life of the process: do not use this call
+ *     on a device after cudaDeviceReset (the array's module is reloaded and
+ *     the kept address may no longer be valid).
  *   - Every call on a device shares the one array, which keeps the contents
  *     the last call left; the counters a step needs zeroed are reset by the
  *     step itself.  Calls that overlap on the device (other streams, other
@@ -436,6 +440,12 @@ ION_API int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N,
  * synchronizes (about 0.1 s).  The paper has no counterpart.
  * Errors: ION_EINVAL, ION_ECUDA. */
 ION_API int ion_measure_peaks(double* out);
+
+/* ion_binary_version -- the compute capability the library's device code
+ * was compiled for, as the CUDA runtime reports it for the loaded module
+ * (major * 10 + minor: 103 for sm_103a), or ION_ECUDA if the current device
+ * cannot load it.  A build check; the paper has no counterpart. */
+ION_API int ion_binary_version(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 ION_API const char* ion_last_error(void);

@@ -29,7 +29,7 @@
  *      level is below eps_shift (Sec. 3, text after Fig. 2 and after Eq. 9),
  *      at most w-1 times and only while hi < Z.
  *
- * Readings of the paper taken here (each is listed in the design doc):
+ * Readings of the paper taken here (where it is silent or ambiguous):
  *   - Q = k+1 for the rate W_k of state k -> k+1 ("charge number after
  *     ionization", text after Eq. 1).
  *   - E_L is the magnitude |E| given per cell; Eq. 1 is applied as printed

@@ -17,7 +17,7 @@ namespace ion {
 //   a2 = log2(A) + b log2(E_a),
 //   A  = w_a sqrt(3 n*^3/(pi Q^3)) Q^2/(2 n*^2) (2e/n*)^(2n*) f(l,m)/(2 pi n*)
 //        (2 Q^3/n*^3)^(2n* - |m| - 1).
-// Built once per species on the host in double (species.cu).
+// Built once per species on the host in double (api.cu, build_table).
 // ---------------------------------------------------------------------------
 struct SpeciesTable {
   int Z;

@@ -108,7 +108,15 @@ struct LaunchShape {
   int blocks_per_sm;    // 0: as many as fit
 };
 
-// Workspace layout (step_f32.cu).
+// Workspace layout of the FP32 form (bound by bind_workspace, step_f32.cu):
+// the header, the FP64-coefficient queue (cell, job) and the stiff-cell
+// records (cell, job, |E|, lo | hi << 8, ION_MAX_WINDOW planes), each
+// section 256-byte aligned.  The FP64 form uses the header alone.
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t f32_workspace_bytes(size_t n) {
+  return kHdrBytes + round256(4 * n) + round256(n) + round256(4 * n) + round256(n) +
+         round256(4 * n) + round256(2 * n) + round256(4 * n * ION_MAX_WINDOW);
+}
 size_t step_workspace_bytes(int64_t ncells, bool f64);
 void bind_workspace(Scratch& s, void* ws, int64_t ncells);
 

@@ -11,6 +11,9 @@ namespace {
 constexpr int64_t kMaxCells = ION_STEP_NOALLOC_MAX_CELLS;
 constexpr size_t kScratchBytes = ION_STEP_NOALLOC_SCRATCH_BYTES;
 constexpr int kMaxDevices = 64;
+static_assert(ion::f32_workspace_bytes(kMaxCells) == kScratchBytes,
+              "ION_STEP_NOALLOC_SCRATCH_BYTES must equal the FP32 workspace of "
+              "ION_STEP_NOALLOC_MAX_CELLS cells");
 
 // One array per device that loads the library; its size covers
 // ion_step_workspace_bytes(kMaxCells, ION_F32).

@@ -132,3 +132,12 @@ extern "C" int ion_measure_peaks(double* out) {
   out[3] = threads * it_dexp * kChains / (ms[3] * 1e-3);      // FP64 exp2 / s
   return ion::set_error(ION_OK, "%s", "");
 }
+
+extern "C" int ion_binary_version(void) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, sfu_ex2_loop);
+  if (e != cudaSuccess)
+    return ion::set_error(ION_ECUDA, "ion_binary_version: %s", cudaGetErrorString(e));
+  ion::set_error(ION_OK, "%s", "");
+  return fa.binaryVersion;
+}

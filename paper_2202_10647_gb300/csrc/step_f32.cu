@@ -725,8 +725,6 @@ __global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ Bat
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t round256(size_t x) { return (x + 255) / 256 * 256; }
-
 // One instantiation of the streaming kernel: its function and smem needs.
 struct StreamVariant {
   const void* fn;
@@ -800,10 +798,7 @@ bool valid_shape(const LaunchShape& s) {
 }
 
 size_t step_workspace_bytes(int64_t ncells, bool f64) {
-  if (f64) return kHdrBytes;
-  const size_t n = (size_t)ncells;
-  return kHdrBytes + round256(4 * n) + round256(n) + round256(4 * n) + round256(n) +
-         round256(4 * n) + round256(2 * n) + round256(4 * n * ION_MAX_WINDOW);
+  return f64 ? kHdrBytes : f32_workspace_bytes((size_t)ncells);
 }
 
 void bind_workspace(Scratch& s, void* ws, int64_t ncells) {

@@ -40,7 +40,8 @@ EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
            "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
            "ion_surrogate_create", "ion_surrogate_destroy", "ion_surrogate_rates",
-           "ion_step_surrogate", "ion_measure_peaks", "ion_last_error")
+           "ion_step_surrogate", "ion_measure_peaks", "ion_binary_version",
+           "ion_last_error")
 
 #: forward pass in the tensor-core arithmetic (bf16 W2, W3, h1, h2; SFU tanh)
 ION_MLP_BF16 = 0x1
@@ -184,6 +185,8 @@ def _declare(lib):
                                        _vp, ctypes.c_size_t, _vp]
     lib.ion_measure_peaks.restype = ctypes.c_int
     lib.ion_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    lib.ion_binary_version.restype = ctypes.c_int
+    lib.ion_binary_version.argtypes = []
     lib.ion_step_noalloc.restype = ctypes.c_int
     lib.ion_step_noalloc.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                      _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_int, _vp]
@@ -368,6 +371,10 @@ def step_noalloc(sp: Species, E: torch.Tensor, N: torch.Tensor, k_lo: torch.Tens
     if N.dim() != 2 or N.shape[0] != sp.Z + 1:
         raise ValueError(f"N must have shape (Z+1, ld) = ({sp.Z + 1}, ld)")
     n = E.numel() if ncells is None else int(ncells)
+    if n < 0 or n > min(E.numel(), k_lo.numel(), k_hi.numel(), dne.numel(), N.shape[1]):
+        raise ValueError("ncells outside the arrays")
+    if n_gas is not None and n > n_gas.numel():
+        raise ValueError("ncells outside n_gas")
     opts = _opts(eps_shift, degen_gap, window)
     _check(lib().ion_step_noalloc(sp.handle, _ptr(E), _ptr(N), N.shape[1], n, float(dt),
                                   _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),

@@ -1,6 +1,6 @@
 """Run a few steps on a reduced copy of a benchmark workload, for profilers.
 
-  python -m paper_2202_10647_gb300.profile_step [--nz 64]
+  python profile_step.py [--nz 64]
         [--form f32|f64|both|surrogate|argon] [--steps 3] [--train-steps 1000]
 
 f32/f64: the nitrogen 3D workload on nz x 256 x 512 cells (x fastest) of the
@@ -17,7 +17,7 @@ import argparse
 
 import torch
 
-from . import ionize, workloads
+from paper_2202_10647_gb300 import ionize, workloads
 
 
 def main():
@@ -47,7 +47,7 @@ def main():
               "stiff cells:", ionize.stiff_cells(ws), "of", n)
         return
     if args.form == "surrogate":
-        from . import surrogate
+        from paper_2202_10647_gb300 import surrogate
         sd = workloads.argon_like()
         sp = ionize.Species(sd.U, sd.l, sd.m)
         net, _, _ = surrogate.build(sp, steps=args.train_steps)

@@ -48,7 +48,8 @@ def test_batched_every_shape_matches_oracle(shape):
     ws = ionize.step_batched(jobs, 0.05, shape=(shape[0], shape[1], 0))
     torch.cuda.synchronize()
     for wl, job in zip(wls, jobs):
-        check(gpu_out(job), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F32)
+        check(gpu_out(job), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F32, sd=wl.species,
+              E=wl.E.double().numpy())
     assert ionize.counters(ws)[1] == 0
 
 
@@ -71,7 +72,8 @@ def test_batched_fp64_form():
     ionize.step_batched(j64, 0.05, flags=ionize.ION_F64_PLAIN)
     torch.cuda.synchronize()
     for wl, job in zip(wls, j64):
-        check(gpu_out(job), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F64_PLAIN)
+        check(gpu_out(job), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F64_PLAIN, sd=wl.species,
+              E=wl.E.double().numpy())
 
 
 def test_autotune_returns_a_built_shape():

@@ -57,4 +57,5 @@ def test_step(model, consts, flags):
                                      wl.lo.numpy(), wl.hi.numpy())
     out = dict(N=N.double().cpu().numpy(), lo=lo.cpu().numpy(), hi=hi.cpu().numpy(),
                dne=dne.double().cpu().numpy())
-    check(out, dict(N=No, lo=loo, hi=hio, dne=dneo), wl.lo, wl.hi, flags)
+    check(out, dict(N=No, lo=loo, hi=hio, dne=dneo), wl.lo, wl.hi, flags, sd=sd,
+          E=wl.E.to(dt_).double().numpy())

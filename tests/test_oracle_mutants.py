@@ -15,6 +15,17 @@ MUTANTS = {
         "1.0;")],
     # static-field model: the cycle-averaging factor kept
     "static_keeps_sqrt": [("model == 1 ? 1.0 :", "model == 2 ? 1.0 :")],
+    # Eq. 1: the n*-dependent prefactors, each with one power of n* lost
+    "q2_over_2nstar": [("(q * q) / (2.0 * nstar * nstar)", "(q * q) / (2.0 * nstar)")],
+    "flm_divisor_no_nstar": [("(2.0 * M_PI * nstar * pow(2.0, (double)am)",
+                              "(2.0 * M_PI * pow(2.0, (double)am)")],
+    "sqrt_nstar_squared": [("sqrt(3.0 * pow(nstar, 3.0) * E / (M_PI * pow(q, 3.0) * E_a))",
+                            "sqrt(3.0 * pow(nstar, 2.0) * E / (M_PI * pow(q, 3.0) * E_a))")],
+    # Eq. 1: (2e/n*)^(2n*) with the wrong exponent
+    "power_2e_nstar": [("pow(2.0 * e / nstar, 2.0 * nstar)", "pow(2.0 * e / nstar, nstar)")],
+    # Eq. 1: (l-|m|)! in the f(l,m) divisor replaced by l!
+    "flm_l_minus_m": [("or_factorial(am) *\n           or_factorial(l - am))",
+                       "or_factorial(am) *\n           or_factorial(l))")],
     # Eq. 1: sign of the tunnelling exponent
     "exponent_sign": [("      exp(-expo) *", "      exp(expo) *")],
     # Eq. 1: Q taken as the charge before ionization
@@ -43,6 +54,10 @@ MUTANTS = {
 PIN_TESTS = [
     (P.test_adk_hydrogen_closed_form, (510.0,)),
     (P.test_adk_hydrogenic_ion_closed_form, (1500.0,)),
+    (P.test_adk_nstar_two_closed_form, (400.0, 0)),
+    (P.test_adk_nstar_two_closed_form, (400.0, 1)),
+    (P.test_adk_nstar_two_d_state_closed_form, (900.0, 1, 0)),
+    (P.test_adk_f_state_m_two_closed_form, (2000.0,)),
     (P.test_adk_m_projection_ratio, (2, 300.0)),
     (P.test_adk_log_slope, (1, 800.0)),
     (P.test_adk_static_hydrogen_landau_lifshitz, (300.0,)),

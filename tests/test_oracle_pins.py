@@ -53,6 +53,63 @@ def test_adk_hydrogenic_ion_closed_form(E):
     assert got == pytest.approx(want, rel=1e-13)
 
 
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("E", [60.0, 400.0, 3000.0])
+def test_adk_nstar_two_closed_form(E, model):
+    # Q = 1, U = U_H/4, l = m = 0  =>  n* = 2, where every power of n* in
+    # Eq. 1 counts.  Term by term:
+    #   sqrt(3 n*^3 E/(pi Q^3 E_a)) = sqrt(24 E/(pi E_a))
+    #   Q^2/(2 n*^2)                = 1/8
+    #   (2e/n*)^(2n*)               = e^4
+    #   f(0,0)/(2 pi n*)            = 1/(4 pi)
+    #   (2 E_a Q^3/(E n*^3))^(2n*-1) = (E_a/(4E))^3
+    #   exp(-(2/3)(Q/n*)^3 E_a/E)    = exp(-E_a/(12 E))
+    # so W = w_a sqrt(24E/(pi E_a)) e^4/(2048 pi) (E_a/E)^3 exp(-E_a/(12E));
+    # the static-field model (model 1) drops the square root.
+    cyc = 1.0 if model == 1 else math.sqrt(24 * E / (math.pi * E_A))
+    want = (OMEGA_A * cyc * math.e ** 4 / (2048 * math.pi) * (E_A / E) ** 3
+            * math.exp(-E_A / (12 * E))) * 1e-15
+    got = oracle.adk_rate(E, U_H / 4, 0, 0, 1, model=model)
+    assert got == pytest.approx(want, rel=1e-13)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("m", [1, -1])
+@pytest.mark.parametrize("E", [150.0, 900.0, 5000.0])
+def test_adk_nstar_two_d_state_closed_form(E, m, model):
+    # Q = 2, U = U_H, l = 2, |m| = 1  =>  n* = 2 and f(2,1) = 15.  Term by
+    # term:
+    #   sqrt(3 n*^3 E/(pi Q^3 E_a)) = sqrt(3 E/(pi E_a))
+    #   Q^2/(2 n*^2)                = 1/2
+    #   (2e/n*)^(2n*)               = e^4
+    #   f(2,1)/(2 pi n*)            = 15/(4 pi)
+    #   (2 E_a Q^3/(E n*^3))^(2n*-|m|-1) = (2 E_a/E)^2
+    #   exp(-(2/3)(Q/n*)^3 E_a/E)    = exp(-2 E_a/(3 E))
+    # so W = w_a sqrt(3E/(pi E_a)) (15 e^4/(2 pi)) (E_a/E)^2 exp(-2E_a/(3E)).
+    cyc = 1.0 if model == 1 else math.sqrt(3 * E / (math.pi * E_A))
+    want = (OMEGA_A * cyc * 15 * math.e ** 4 / (2 * math.pi) * (E_A / E) ** 2
+            * math.exp(-2 * E_A / (3 * E))) * 1e-15
+    got = oracle.adk_rate(E, U_H, 2, m, 2, model=model)
+    assert got == pytest.approx(want, rel=1e-13)
+
+
+@pytest.mark.parametrize("E", [300.0, 2000.0])
+def test_adk_f_state_m_two_closed_form(E):
+    # Q = 3, U = 9 U_H/4, l = 3, |m| = 2  =>  n* = 3/(3/2) = 2, f(3,2) =
+    # 7 * 5! / (4 * 2! * 1!) = 105.  Term by term:
+    #   sqrt(3 n*^3 E/(pi Q^3 E_a)) = sqrt(24 E/(27 pi E_a)) = sqrt(8E/(9 pi E_a))
+    #   Q^2/(2 n*^2)                = 9/8
+    #   (2e/n*)^(2n*)               = e^4
+    #   f/(2 pi n*)                 = 105/(4 pi)
+    #   (2 E_a Q^3/(E n*^3))^(2n*-|m|-1) = (27 E_a/(4 E))^1
+    #   exp(-(2/3)(Q/n*)^3 E_a/E)    = exp(-(2/3)(27/8) E_a/E) = exp(-9 E_a/(4E))
+    want = (OMEGA_A * math.sqrt(8 * E / (9 * math.pi * E_A)) * (9 / 8) * math.e ** 4
+            * 105 / (4 * math.pi) * (27 * E_A / (4 * E)) * math.exp(-9 * E_A / (4 * E))) * 1e-15
+    for m in (2, -2):
+        got = oracle.adk_rate(E, 9 * U_H / 4, 3, m, 3)
+        assert got == pytest.approx(want, rel=1e-13)
+
+
 @pytest.mark.parametrize("k", range(7))
 @pytest.mark.parametrize("E", [300.0, 2500.0])
 def test_adk_m_projection_ratio(k, E):
