@@ -244,6 +244,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _r(x, nd=4):
+    return None if x is None else float(f"{x:.{nd}g}")
+
+
+def summary_of(line):
+    """ms per step, G cell-updates/s and roofline fraction of each form."""
+    f = line["forms"]
+    out = {"fp32_nitrogen": {"ms": _r(line["ms_per_step"]), "Gcells_s": _r(line["value"] / 1e9),
+                             "frac_hbm": _r(line["roofline"]["frac"], 3)}}
+    p = f.get("fp64_plain")
+    if p:
+        out["fp64_plain_nitrogen"] = {"ms": _r(p["ms_per_step"]), "Gcells_s": _r(p["value"] / 1e9),
+                                      "frac_fp64_exp2": _r(p["roofline"]["frac"], 3)}
+    b = f.get("batched_mixed_species")
+    if b:
+        out["batched_30M"] = {"ms": _r(b["ms_per_step"]), "Gcells_s": _r(b["value"] / 1e9),
+                              "frac_hbm": _r(b["frac_of_hbm_peak"], 3),
+                              "err": _r(b["max_abs_err_N_vs_oracle"], 2)}
+        if b.get("roofline"):
+            out["batched_30M"]["frac_issue"] = _r(b["roofline"]["frac"], 3)
+    s = f.get("surrogate_argon")
+    if s:
+        out["surrogate_argon"] = {"ms": _r(s["ms_per_step"]),
+                                  "plain_ms": _r(s["plain_fp32"]["ms_per_step"]),
+                                  "gain": _r(s["gain_vs_plain"], 3),
+                                  "on_network": _r(s["cells_on_network_rates"], 3),
+                                  "rate_err_median": _r((s.get("accuracy") or {}).get(
+                                      "median_rel_rate_error"), 3)}
+    k = f.get("krypton_beams_50_steps_graph")
+    if k:
+        out["krypton_50_steps"] = {"ms_with_check": _r(k["ms_per_50_steps"]),
+                                   "ms_steps_only": _r(k["ms_per_50_steps_steps_only"]),
+                                   "ms_adaptive": _r(k["adaptive_window_steps_only"]["ms_per_50_steps"]),
+                                   "ms_surrogate": _r((k.get("surrogate_form") or {}).get(
+                                       "ms_per_50_steps")),
+                                   "max_sum_err": _r(k["max_abs_sum_N_minus_1"]["max"], 2)}
+    if line.get("e2e"):
+        out["e2e_ms"] = _r(line["e2e"]["ms_per_step"])
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -758,6 +799,9 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
     }
+    # the headline numbers of every form again, compact and last on the line
+    # (a reader of the line's tail sees them all)
+    line["summary"] = summary_of(line)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

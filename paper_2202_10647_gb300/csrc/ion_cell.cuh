@@ -31,6 +31,17 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
                  "n"(BYTES)
                  : "memory");
 }
+// The same with the shared-memory destination as a 32-bit shared address.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_s(uint32_t s, const void* gmem) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem),
+                 "n"(BYTES)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }

@@ -141,9 +141,12 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 // 6e-7) are recomputed in float-float.  The Taylor series runs the warp's
 // largest term count (extra terms only add accuracy), counted by one ballot:
 // lane i holds thr_lane = kThrF32[i] (infinity from lane kEasyTerms on).
+template <int Q>
+using PlaneRows = typename VecOf<Q>::T[ION_MAX_WINDOW][32];
+
 template <int Q, int WM, bool AD>
 __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
-                                           const StagedF32& tab, const QStage<Q>& st,
+                                           const StagedF32& tab, const PlaneRows<Q>& P,
                                            int lane, int c0, const float (&Ev)[Q],
                                            const int (&lo)[Q], const int (&hi)[Q],
                                            const bool (&ok)[Q], bool uni, bool (&stiff)[Q], float thr_lane) {
@@ -153,7 +156,7 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
   for (int j = 0; j < Q; ++j) w[j] = ok[j] ? hi[j] - lo[j] + 1 : 0;
 #pragma unroll
   for (int r = 0; r < WM; ++r) {
-    const typename VecOf<Q>::T p = st.P[r][lane];
+    const typename VecOf<Q>::T p = P[r][lane];
 #pragma unroll
     for (int j = 0; j < Q; ++j) v[j][r] = vget(p, j);  // r >= w: ignored
   }
@@ -314,6 +317,40 @@ constexpr size_t stream_smem(int njobs) {
 template <int Q>
 constexpr int stream_regs() {
   return Q == 1 ? 64 : Q == 2 ? 80 : 128;
+}
+
+// Each job's last, partial chunk (ncells % kChunk cells), taken by one warp
+// per job (gw of TW): every valid cell becomes a record for the stiff
+// kernel, which runs the full path.
+__device__ __forceinline__ void tail_records(const BatchArgs& a, int kChunk, int gw, int TW,
+                                             int lane) {
+  for (int jid = 0; jid < a.njobs; ++jid) {
+    if (gw != (TW - 1 - jid % TW)) continue;
+    const JobIO& J = a.job[jid];
+    const int tail0 = (J.ncells / kChunk) * kChunk;
+    for (int cb = tail0; cb < J.ncells; cb += 32) {
+      const int c = cb + lane;
+      bool take = false;
+      float Ec = 0.0f, v[ION_MAX_WINDOW];
+      int lo = 0, hi = 0;
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = 0.0f;
+      if (c < J.ncells) {
+        Ec = static_cast<const float*>(J.E)[c];
+        lo = J.lo[c];
+        hi = J.hi[c];
+        take = window_ok(lo, hi, J.Z);
+        if (!take) atomicAdd(&a.ws.hdr[kHdrInvalid], 1u);
+        const float* p = static_cast<const float*>(J.N) + (int64_t)lo * J.ld + c;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+          if (take && r < hi - lo + 1) v[r] = p[0];
+          p += J.ld;
+        }
+      }
+      append_record(a.ws, take, jid, c, Ec, lo, hi, v);
+    }
+  }
 }
 
 // AD: the adaptive window policy (a separate instantiation, so that the
@@ -534,11 +571,11 @@ __global__ void __maxnreg__(stream_regs<Q>())
         }
       }
     } else if (WMw == 2) {
-      easy_cells<Q, 2, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
+      easy_cells<Q, 2, AD>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
     } else if (WMw <= 4) {
-      easy_cells<Q, 4, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
+      easy_cells<Q, 4, AD>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
     } else {
-      easy_cells<Q, 6, AD>(J, a.pol, tab, st, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
+      easy_cells<Q, 6, AD>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
     }
     // stiff cells: their inputs (as loaded) go to the record queue
     bool any = false;
@@ -557,35 +594,279 @@ __global__ void __maxnreg__(stream_regs<Q>())
   }
   cp_async_wait<0>();
 
-  // each job's last, partial chunk (ncells % (32 Q) cells): every valid cell
-  // becomes a record for the stiff kernel, which runs the full path
-  for (int jid = 0; jid < a.njobs; ++jid) {
-    if (gw != (TW - 1 - jid % TW)) continue;
-    const JobIO& J = a.job[jid];
-    const int tail0 = (J.ncells / kChunk) * kChunk;
-    for (int cb = tail0; cb < J.ncells; cb += 32) {
-      const int c = cb + lane;
-      bool take = false;
-      float Ec = 0.0f, v[ION_MAX_WINDOW];
-      int lo = 0, hi = 0;
+  tail_records(a, kChunk, gw, TW, lane);
+}
+
+// ---------------------------------------------------------------------------
+// ion_lean_kernel<Q, W>: the streaming kernel for one species under the
+// paper's window rule (ion_step's common case) with less bookkeeping per
+// chunk than ion_stream_kernel.  The cell arithmetic is the same
+// (easy_cells, records for stiff cells, the cold-chunk rule).
+//   * A warp's runs of four chunks fill its four stages in order, so the
+//     chunk of a stage follows from three run bases kept in registers: the
+//     run being computed, the one whose planes are requested and the one
+//     whose |E| and windows are requested.  Nothing is stored per stage.
+//   * |E|, k_lo and k_hi of a chunk arrive as 16-byte copies, one per lane
+//     (lanes [0, 8Q) |E|, then k_lo, then k_hi), each lane's source moving
+//     by a fixed stride from chunk to chunk.
+//   * Whether a chunk is cold is decided when its planes are requested (its
+//     |E| and windows are then in shared memory).  A cold chunk brings in
+//     only the lowest window plane of each cell, which is what the slide
+//     test reads; where that state holds less than eps_shift the planes
+//     above it are read directly.
+//   * Element offsets into the planes are 32-bit ((Z+1) ld < 2^32).
+// ---------------------------------------------------------------------------
+template <int Q>
+struct LStage {
+  using V = typename VecOf<Q>::T;
+  V E[32];                  // |E| of the chunk's 32 Q cells, Q per lane
+  uint8_t lo[32 * Q];       // k_lo
+  uint8_t hi[32 * Q];       // k_hi
+  V P[ION_MAX_WINDOW][32];  // P[r][lane] component j = N[lo_j + r] of cell j
+};
+static_assert(sizeof(LStage<1>) % 16 == 0 && sizeof(LStage<2>) % 16 == 0,
+              "stages keep the 16-byte alignment of the front copies");
+
+template <int Q, int W>
+constexpr size_t lean_smem() {
+  return sizeof(StagedF32) + (size_t)W * kStages * sizeof(LStage<Q>);
+}
+
+template <int Q, int W>
+__global__ void __maxnreg__(stream_regs<Q>())
+    ion_lean_kernel(const __grid_constant__ BatchArgs a) {
+  static_assert(Q == 1 || Q == 2, "one 16-byte front copy per lane at most");
+  static_assert(kRun == kStages, "a run of chunks fills the stages in order");
+  using V = typename VecOf<Q>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  StagedF32& tab = *reinterpret_cast<StagedF32*>(smem);
+  LStage<Q>* ring = reinterpret_cast<LStage<Q>*>(smem + sizeof(StagedF32));
+  const JobIO& J = a.job[0];
+  stage_f32(J.tab, a.pol.log2dt, &tab);
+  if (threadIdx.x < 32) stage_cold(J.tab, a.pol.log2dt, kColdLog2, tab.ecold, threadIdx.x);
+  {
+    // plane slots past a cell's window are read (and ignored); keep them
+    // finite
+    float* z = reinterpret_cast<float*>(ring);
+    const int nz = (int)(W * kStages * sizeof(LStage<Q>) / sizeof(float));
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) z[i] = 0.0f;
+  }
+  __syncthreads();
+
+  constexpr int kChunk = 32 * Q;
+  constexpr uint32_t kStageBytes = sizeof(LStage<Q>);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  LStage<Q>* S = ring + wib * kStages;
+  const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(S);
+  const int gw = blockIdx.x * W + wib;
+  const int TW = gridDim.x * W;
+  const uint32_t nchunks = (uint32_t)a.nchunks;
+  const float* __restrict__ Nf = static_cast<const float*>(J.N);
+  const uint32_t ld = (uint32_t)J.ld;
+  const int Z = J.Z;
+
+  // this lane's front copy: its source at chunk 0, the source's stride per
+  // chunk and its offset in a stage
+  const bool f_on = lane < 12 * Q;
+  const char* f_src;
+  uint32_t f_stride, f_dst;
+  if (lane < 8 * Q) {
+    f_src = static_cast<const char*>(J.E) + 16 * lane;
+    f_stride = 4 * kChunk;
+    f_dst = (uint32_t)offsetof(LStage<Q>, E) + 16 * lane;
+  } else if (lane < 10 * Q) {
+    f_src = reinterpret_cast<const char*>(J.lo) + 16 * (lane - 8 * Q);
+    f_stride = kChunk;
+    f_dst = (uint32_t)offsetof(LStage<Q>, lo) + 16 * (lane - 8 * Q);
+  } else {
+    f_src = reinterpret_cast<const char*>(J.hi) + 16 * (lane - 10 * Q);
+    f_stride = kChunk;
+    f_dst = (uint32_t)offsetof(LStage<Q>, hi) + 16 * (lane - 10 * Q);
+  }
+  const uint32_t p_dst = (uint32_t)offsetof(LStage<Q>, P) + (uint32_t)sizeof(V) * lane;
+
+  uint32_t* const next = &a.ws.hdr[kHdrChunk];
+  auto fetch_run = [&]() -> uint32_t {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(next, (unsigned)kRun);
+    return __shfl_sync(kFull, b, 0);
+  };
+  auto issue_front = [&](int s, uint32_t g) {
+    if (g < nchunks && f_on)
+      cp_async_s<16>(s_base + s * kStageBytes + f_dst, f_src + (size_t)g * f_stride);
+    cp_async_commit();
+  };
+  // bit s: the chunk in stage s is cold (every cell below its cold field)
+  uint32_t coldm = 0;
+  auto issue_planes = [&](int s, uint32_t g) {
+    if (g < nchunks) {
+      const LStage<Q>& st = S[s];
+      const uint32_t l = lane_bytes<Q>(reinterpret_cast<const uint32_t*>(st.lo), lane);
+      const uint32_t h = lane_bytes<Q>(reinterpret_cast<const uint32_t*>(st.hi), lane);
+      const V e = st.E[lane];
+      int lo[Q], w[Q];
+      bool c = true;
 #pragma unroll
-      for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = 0.0f;
-      if (c < J.ncells) {
-        Ec = static_cast<const float*>(J.E)[c];
-        lo = J.lo[c];
-        hi = J.hi[c];
-        take = window_ok(lo, hi, J.Z);
-        if (!take) atomicAdd(&a.ws.hdr[kHdrInvalid], 1u);
-        const float* p = static_cast<const float*>(J.N) + (int64_t)lo * J.ld + c;
+      for (int j = 0; j < Q; ++j) {
+        lo[j] = (l >> (8 * j)) & 0xff;
+        const int hj = (h >> (8 * j)) & 0xff;
+        w[j] = window_ok(lo[j], hj, Z) ? hj - lo[j] + 1 : 0;
+        c = c && (w[j] <= 1 || fabsf(vget(e, j)) < tab.ecold[min(lo[j], ION_MAX_Z)]);
+      }
+      const bool cold = __all_sync(kFull, c);
+      coldm = cold ? (coldm | (1u << s)) : (coldm & ~(1u << s));
+      const uint32_t c0 = g * (uint32_t)kChunk + (uint32_t)(Q * lane);
+      const uint32_t pd = s_base + s * kStageBytes + p_dst;
+      if (bytes_equal<Q>(l) && bytes_equal<Q>(h)) {
+        const int rows = cold ? min(w[0], 1) : w[0];
+        uint32_t off = (uint32_t)lo[0] * ld + c0;
 #pragma unroll
         for (int r = 0; r < ION_MAX_WINDOW; ++r) {
-          if (take && r < hi - lo + 1) v[r] = p[0];
-          p += J.ld;
+          if (r < rows) cp_async_s<4 * Q>(pd + r * 32 * (uint32_t)sizeof(V), Nf + off);
+          off += ld;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          const int rows = cold ? min(w[j], 1) : w[j];
+          uint32_t off = (uint32_t)lo[j] * ld + c0 + j;
+          for (int r = 0; r < rows; ++r) {
+            cp_async_s<4>(pd + r * 32 * (uint32_t)sizeof(V) + 4 * j, Nf + off);
+            off += ld;
+          }
         }
       }
-      append_record(a.ws, take, jid, c, Ec, lo, hi, v);
     }
+    cp_async_commit();
+  };
+
+  const float thr_lane = lane < kEasyTerms ? kThrF32[lane] : __int_as_float(0x7f800000);
+  // Chunk k lives in stage k mod 4, and the wait discipline is that of
+  // ion_stream_kernel: fronts three chunks ahead, planes two.
+  uint32_t run_next = fetch_run();
+  uint32_t run_mid = run_next, run_cur = run_next;
+  issue_front(0, run_next);
+  issue_front(1, run_next + 1);
+  issue_front(2, run_next + 2);
+  cp_async_wait<2>();
+  __syncwarp();
+  issue_planes(0, run_mid);
+  cp_async_wait<2>();
+  __syncwarp();
+  issue_planes(1, run_mid + 1);
+  for (int k = 0;; ++k) {
+    const int s3 = (k + 3) & 3, s2 = (k + 2) & 3, s0 = k & 3;
+    if (s3 == 0) run_next = fetch_run();
+    issue_front(s3, run_next + s3);
+    cp_async_wait<2>();  // front(k+2) and planes(k)
+    __syncwarp();
+    if (s2 == 0) run_mid = run_next;
+    issue_planes(s2, run_mid + s2);
+    if (s0 == 0) run_cur = run_mid;
+    const uint32_t g = run_cur + s0;
+    if (g >= nchunks) break;  // runs come in increasing order: no more
+
+    const LStage<Q>& st = S[s0];
+    const int c0 = (int)(g * (uint32_t)kChunk) + Q * lane;
+    const V e = st.E[lane];
+    float Ev[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) Ev[j] = vget(e, j);
+    const uint32_t l = lane_bytes<Q>(reinterpret_cast<const uint32_t*>(st.lo), lane);
+    const uint32_t h = lane_bytes<Q>(reinterpret_cast<const uint32_t*>(st.hi), lane);
+    int lo[Q], hi[Q], wl = 0;
+    bool ok[Q];
+    bool uni;
+    if (bytes_equal<Q>(l) && bytes_equal<Q>(h)) {
+      const int l0 = l & 0xff, h0 = h & 0xff;
+      const bool o = window_ok(l0, h0, Z);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        lo[j] = l0;
+        hi[j] = h0;
+        ok[j] = o;
+      }
+      wl = o ? h0 - l0 + 1 : 0;
+      if (!o) atomicAdd(&a.ws.hdr[kHdrInvalid], (unsigned)Q);
+      uni = o;
+    } else {
+      int nbad = 0;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        lo[j] = (l >> (8 * j)) & 0xff;
+        hi[j] = (h >> (8 * j)) & 0xff;
+        ok[j] = window_ok(lo[j], hi[j], Z);
+        nbad += ok[j] ? 0 : 1;
+        wl = ok[j] ? max(wl, hi[j] - lo[j] + 1) : wl;
+      }
+      if (nbad) atomicAdd(&a.ws.hdr[kHdrInvalid], (unsigned)nbad);
+      uni = false;
+    }
+    bool stiff[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) stiff[j] = false;
+    if ((coldm >> s0) & 1u) {
+      // Cold chunk: N stays as it is and no electron is freed (the series
+      // would take no term); dne is written, and k_lo/k_hi where the window
+      // slides.
+      float* D = static_cast<float*>(J.dne);
+      if (uni) {
+        float z[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) z[j] = 0.0f;
+        vstore(D + c0, z);
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        if (!ok[j]) continue;
+        if (!uni) __stcs(D + c0 + j, 0.0f);
+        const float p0 = vget(st.P[0][lane], j);
+        if ((a.pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi[j] > lo[j] && hi[j] < Z &&
+            p0 < a.pol.eps_f) {
+          // the planes above the lowest were not brought in: read them
+          float v[ION_MAX_WINDOW];
+          v[0] = p0;
+          const float* p = Nf + (uint32_t)lo[j] * ld + (uint32_t)(c0 + j);
+#pragma unroll
+          for (int r = 1; r < ION_MAX_WINDOW; ++r)
+            v[r] = r < hi[j] - lo[j] ? p[(uint32_t)r * ld] : 0.0f;
+          int nl = lo[j], nh = hi[j];
+          slide_window<float, ION_MAX_WINDOW>(v, hi[j] - lo[j] + 1, Z, a.pol.eps_f, nl, nh);
+          J.lo[c0 + j] = (uint8_t)nl;
+          J.hi[c0 + j] = (uint8_t)nh;
+        }
+      }
+    } else {
+      const int WMw = __reduce_max_sync(kFull, wl);
+      if (WMw <= 2)
+        easy_cells<Q, 2, false>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
+                                thr_lane);
+      else if (WMw <= 4)
+        easy_cells<Q, 4, false>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
+                                thr_lane);
+      else
+        easy_cells<Q, 6, false>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
+                                thr_lane);
+      // stiff cells: their inputs (as loaded) go to the record queue
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) any = any || stiff[j];
+      if (__ballot_sync(kFull, any)) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          float vin[ION_MAX_WINDOW];
+#pragma unroll
+          for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = vget(st.P[r][lane], j);
+          append_record(a.ws, stiff[j], 0, c0 + j, Ev[j], lo[j], hi[j], vin);
+        }
+      }
+    }
+    __syncwarp();
   }
+  cp_async_wait<0>();
+
+  tail_records(a, kChunk, gw, TW, lane);
 }
 
 // The stiff-cell records, one per thread.  W bounds the width; the window
@@ -730,6 +1011,7 @@ struct StreamVariant {
   const void* fn;
   int Q, W;
   bool adaptive;
+  bool lean;  // ion_lean_kernel (one species, the paper's window rule)
   size_t (*smem)(int);
 };
 
@@ -738,20 +1020,42 @@ size_t smem_of(int njobs) {
   return stream_smem<Q, W>(njobs);
 }
 
+template <int Q, int W>
+size_t lean_smem_of(int) {
+  return lean_smem<Q, W>();
+}
+
 #define ION_VARIANT(Q, W, AD) \
-  { reinterpret_cast<const void*>(&ion_stream_kernel<Q, W, AD>), Q, W, AD, &smem_of<Q, W> }
+  { reinterpret_cast<const void*>(&ion_stream_kernel<Q, W, AD>), Q, W, AD, false, &smem_of<Q, W> }
 #define ION_VARIANTS(AD)                                                          \
   ION_VARIANT(1, 2, AD), ION_VARIANT(1, 4, AD), ION_VARIANT(1, 8, AD),             \
       ION_VARIANT(2, 2, AD), ION_VARIANT(2, 4, AD), ION_VARIANT(2, 8, AD),         \
       ION_VARIANT(4, 2, AD), ION_VARIANT(4, 4, AD), ION_VARIANT(4, 8, AD)
-const StreamVariant kVariants[] = {ION_VARIANTS(false), ION_VARIANTS(true)};
+#define ION_LEAN(Q, W) \
+  { reinterpret_cast<const void*>(&ion_lean_kernel<Q, W>), Q, W, false, true, &lean_smem_of<Q, W> }
+const StreamVariant kVariants[] = {ION_VARIANTS(false), ION_VARIANTS(true),
+                                   ION_LEAN(1, 2), ION_LEAN(1, 4), ION_LEAN(1, 8),
+                                   ION_LEAN(2, 2), ION_LEAN(2, 4), ION_LEAN(2, 8)};
+#undef ION_LEAN
 #undef ION_VARIANTS
 #undef ION_VARIANT
 
-const StreamVariant* find_variant(int Q, int W, bool adaptive = false) {
+const StreamVariant* find_variant(int Q, int W, bool adaptive = false, bool lean = false) {
   for (const auto& v : kVariants)
-    if (v.Q == Q && v.W == W && v.adaptive == adaptive) return &v;
+    if (v.Q == Q && v.W == W && v.adaptive == adaptive && v.lean == lean) return &v;
   return nullptr;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// The lean kernel serves a launch of one species under the paper's window
+// rule whose arrays allow its copies: 16-byte aligned |E|, k_lo and k_hi,
+// vector-aligned planes, and plane offsets that fit 32 bits.
+bool lean_fits(const BatchArgs& a, int Q) {
+  if (a.njobs != 1 || a.pol.adaptive || (Q != 1 && Q != 2)) return false;
+  const JobIO& J = a.job[0];
+  return J.vec && aligned16(J.E) && aligned16(J.lo) && aligned16(J.hi) &&
+         (uint64_t)(J.Z + 1) * (uint64_t)J.ld < (uint64_t(1) << 32);
 }
 
 // Resident blocks per SM of a variant with `njobs` staged tables, set up and
@@ -825,7 +1129,8 @@ void bind_workspace(Scratch& s, void* ws, int64_t ncells) {
 cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms,
                              cudaStream_t s) {
   const StreamVariant* v =
-      find_variant(shape.cells_per_lane, shape.warps_per_block, a.pol.adaptive != 0);
+      find_variant(shape.cells_per_lane, shape.warps_per_block, a.pol.adaptive != 0,
+                   lean_fits(a, shape.cells_per_lane));
   if (!v) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.ws.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;

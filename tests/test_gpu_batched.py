@@ -122,3 +122,38 @@ def test_full_size_mixed_batch_sampled():
         No, loo, hio, dneo = oracle.step(oracle_species(w.species), Es, Ns, 0.05, ls, hs)
         err = np.abs(w.N[:, ix].double().cpu().numpy() - No).max()
         assert err <= 2e-6, (w.species.name, err)
+
+
+@pytest.mark.parametrize("shape", [(1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (2, 8)])
+@pytest.mark.parametrize("name", ["nitrogen_3d", "Kr-like"])
+def test_single_species_kernel_equals_general_kernel(shape, name):
+    """A launch of one species under the paper's window rule takes the
+    single-species streaming kernel; the same cells launched beside an empty
+    second job take the general one.  Both run the same cell arithmetic, so
+    the results are equal bit for bit, and both match the oracle."""
+    if name == "nitrogen_3d":
+        wl = W.nitrogen_3d(8, 32, 64, seed=47)
+    else:
+        wl = W.ladder_cells(W.krypton_like(), 6007, 48, block=64)
+    n = wl.ncells
+    dev = "cuda"
+    sp = ionize.Species(wl.species.U, wl.species.l, wl.species.m)
+    runs = []
+    for extra in (False, True):
+        E, N = wl.E.to(dev), wl.N.to(dev)
+        lo, hi = wl.lo.clone().to(dev), wl.hi.clone().to(dev)
+        dne = torch.full((n,), 9.0, device=dev)
+        jobs = [(sp, E, N, lo, hi, dne)]
+        if extra:
+            z8 = torch.zeros(4, dtype=torch.uint8, device=dev)
+            jobs.append((sp, torch.zeros(0, device=dev), torch.zeros((wl.species.Z + 1, 4), device=dev),
+                         z8[:0], z8[:0], torch.zeros(0, device=dev)))
+        ws = ionize.step_batched(jobs, 0.05, shape=(shape[0], shape[1], 0))
+        torch.cuda.synchronize()
+        runs.append((N, lo, hi, dne, ionize.counters(ws)))
+    (Na, la, ha, da, ca), (Nb, lb, hb, db, cb) = runs
+    assert torch.equal(Na, Nb) and torch.equal(la, lb) and torch.equal(ha, hb)
+    assert torch.equal(da, db) and ca == cb
+    check(dict(N=Na.double().cpu().numpy(), lo=la.cpu().numpy(), hi=ha.cpu().numpy(),
+               dne=da.double().cpu().numpy()), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F32,
+          sd=wl.species, E=wl.E.double().numpy())

@@ -118,12 +118,15 @@ def forward_bf16(P, K, x):
 def test_tensor_core_network_matches_oracle_with_bf16_rounding(Z, n):
     """The tcgen05 network element by element against the FP64 reference
     network with bf16 rounding of W2, W3, h1 and h2 written in.  What is left
-    is the SFU tanh of the GELU (tanh.approx.f32, error about 2^-11), which
-    can move a hidden activation across a bf16 rounding boundary (one bf16
-    ulp, 2^-7 relative); a model of that (the reference with its tanh
-    perturbed uniformly by up to 2^-10, 20,000 inputs, K = 7..63) deviates
-    by at most 1.9e-2 per output, 7e-3 at the 99th percentile and 1.1e-3 in
-    the median.  Tolerances: twice those."""
+    is the SFU tanh of the GELU (tanh.approx.f32) and the FP32 sums: where
+    the approximate tanh moves a hidden activation across a bf16 rounding
+    boundary, that activation differs by one bf16 ulp (2^-7 relative), and
+    the outputs by up to about 1e-2.  A model of the worst case (the
+    reference with its tanh perturbed uniformly by up to 2^-10) deviates by
+    at most 1.9e-2 per output; on the GB300 the deviation is at most 9e-3,
+    3.5e-4 at the 99th percentile and 5e-8 in the median (no flip in most
+    outputs).  Tolerances: 2e-2 per output, 2e-3 at the 99th percentile,
+    1e-6 in the median."""
     sd = W.synthetic_ladder(Z, 90 + Z)
     sp = gpu_species(sd)
     P32 = torch.tensor(rand_P(Z, 7 * Z, 0.3), dtype=torch.float32)
@@ -142,9 +145,9 @@ def test_tensor_core_network_matches_oracle_with_bf16_rounding(Z, n):
     print(f"Z={Z}: |tensor cores - bf16 reference| max {d.max():.2e}, p99 "
           f"{np.quantile(d, 0.99):.2e}, median {np.median(d):.2e}; against the plain "
           f"FP64 network max {plain.max():.2e}, median {np.median(plain):.2e}")
-    assert d.max() <= 4e-2
-    assert np.quantile(d, 0.99) <= 1.5e-2
-    assert np.median(d) <= 2.5e-3
+    assert d.max() <= 2e-2
+    assert np.quantile(d, 0.99) <= 2e-3
+    assert np.median(d) <= 1e-6
 
 
 @pytest.fixture(scope="module")
