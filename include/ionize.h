@@ -55,6 +55,11 @@ extern "C" {
 #define ION_NO_FP64_FALLBACK 0x4 /* ION_F32 only: FP32 coefficients for all   */
 #define ION_FORCE_FP64_COEF 0x8  /* ION_F32 only: FP64 coefficients for every */
                                  /* cell that takes the Bateman form          */
+#define ION_CONSERVATION_CHECK 0x10 /* measure each cell's change of its total */
+                                 /* population, sum_k N'_k - sum_k N_k (in    */
+                                 /* twice the working precision), and leave   */
+                                 /* the largest |change| in word 10 of the    */
+                                 /* workspace header (float bits)             */
 
 /* ---- dtype codes of ion_rates --------------------------------------------- */
 #define ION_DTYPE_F32 0
@@ -147,8 +152,8 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
  * a 256-byte header plus, for ION_F32, 40 bytes per cell: a 5-byte queue
  * slot (cells whose Bateman coefficients are computed in FP64) and a 35-byte
- * record (cells with a rate W dt > 1, finished by a second kernel from
- * the inputs the first one loaded). */
+ * record (cells with a rate W dt > 1, finished by the record kernel from the
+ * inputs already loaded). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
 
 /* ion_step -- advance the charge-state populations of every cell by one
@@ -187,7 +192,14 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *          whose coefficients were computed in FP64, word 1 the cells left
  *          untouched because their window was invalid (lo > hi, hi > Z or
  *          w > ION_MAX_WINDOW), word 2 the cells that had a rate with
- *          W dt > 1 (finished by the second kernel in the Bateman form).
+ *          W dt > 1 (finished by the record kernel in the Bateman form),
+ *          word 9 (FP32, paper's window rule, |E|, k_lo and k_hi 16-byte
+ *          aligned) the cells some window rate could change (the others
+ *          have every window rate below W dt = 2^-30 and keep N), and with
+ *          ION_CONSERVATION_CHECK word 10 the bits of a float, the largest
+ *          |sum_k N'_k - sum_k N_k| over the cells (the states outside a
+ *          window are not touched, so this is the step's whole conservation
+ *          error; 0 for cells that do not change, NaN if a sum is NaN).
  * Alignment: E, N, dne, n_gas aligned to their element size; with ION_F32
  * k_lo and k_hi 4-byte aligned (they are copied four cells at a time).
  * Calls that share a workspace must not overlap on the device.
@@ -211,7 +223,7 @@ typedef struct {
   const void* n_gas;
 } ion_batch_job;
 
-/* Launch shape of the FP32 streaming kernel: cells per lane (1, 2 or 4),
+/* Launch shape of the FP32 streaming kernels: cells per lane (1, 2 or 4),
  * warps per block (2, 4 or 8), resident blocks per SM (0: as many as fit).
  * NULL selects {2, 8, 0}, which ion_step uses too. */
 typedef struct {
@@ -231,8 +243,8 @@ ION_API size_t ion_step_batched_workspace_bytes(const ion_batch_job* jobs, int n
 /* ion_step_batched -- ion_step for up to ION_MAX_JOBS species (different Z,
  * cell counts and arrays) in one launch: with ION_F32 one persistent kernel
  * walks the cells of every job (each warp picks its job per chunk of cells)
- * and the follow-up kernels serve all jobs; with ION_F64_PLAIN one kernel per
- * job is launched.  Each job obeys the rules of ion_step's arguments; dt,
+ * and the follow-up kernels serve all jobs; with ION_F64_PLAIN one
+ * persistent kernel per job is launched.  Each job obeys the rules of ion_step's arguments; dt,
  * opts and flags apply to all.  `shape` chooses the launch shape (NULL: the
  * default; ion_autotune finds the fastest).  The total cell count must stay
  * below 2^31.  Errors as ion_step. */
@@ -431,6 +443,18 @@ ION_API int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N,
                                float* dne, const float* n_gas, const ion_step_opts* opts,
                                double pop_tol, void* workspace, size_t workspace_bytes,
                                void* stream);
+
+/* ion_surrogate_test_timeout -- test hook of the bounded waits (the paper
+ * has no counterpart).  With on != 0, every later call of this surrogate
+ * (ion_surrogate_rates, ion_step_surrogate) makes the first tensor-core
+ * wait of each tile poll, 64 times, an mbarrier that nothing arrives at, so
+ * that the wait gives up exactly as a wait that ran out of its limit would:
+ * ion_step_surrogate leaves every cell untouched and sets word 5 of the
+ * workspace header, ion_surrogate_rates writes NaN rates, and each CTA waits
+ * (bounded) for the matrix products it skipped before it frees its tensor
+ * memory.  on = 0 restores the normal waits.  Synchronous (one 4-byte copy
+ * to the device).  Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_surrogate_test_timeout(ion_surrogate* s, int on);
 
 /* ion_measure_peaks -- throughput of the current device for the arithmetic
  * the step's forms are bound by, from loops of independent dependency chains

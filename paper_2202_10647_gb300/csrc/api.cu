@@ -232,7 +232,7 @@ namespace {
 
 int check_flags(int flags) {
   const int known = ION_F64_PLAIN | ION_NO_WINDOW_UPDATE | ION_NO_FP64_FALLBACK |
-                    ION_FORCE_FP64_COEF;
+                    ION_FORCE_FP64_COEF | ION_CONSERVATION_CHECK;
   if (flags & ~known) return fail(ION_EINVAL, "unknown flag bits 0x%x", flags & ~known);
   const bool f64 = (flags & ION_F64_PLAIN) != 0;
   if (f64 && (flags & (ION_NO_FP64_FALLBACK | ION_FORCE_FP64_COEF)))

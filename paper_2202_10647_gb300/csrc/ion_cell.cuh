@@ -50,6 +50,34 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// A running sum in twice the working precision (Knuth's TwoSum): the value
+// is s + e.  Used for the change of a window's total population, whose size
+// is that of the rounding of the stored populations.
+template <typename T>
+struct ExactSum {
+  T s = T(0), e = T(0);
+  __device__ __forceinline__ void add(T x) {
+    const T t = s + x;
+    const T z = t - s;
+    e += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ __forceinline__ T value() const { return s + e; }
+};
+
+// The bits of |x| as a float, for a running maximum over non-negative
+// floats (which order like their bits; a NaN is larger than every number).
+template <typename T>
+__device__ __forceinline__ uint32_t abs_bits(T x) {
+  return __float_as_uint(fabsf((float)x));
+}
+
+// The largest of the warp's bits into *word (every lane calls this).
+__device__ __forceinline__ void warp_max_into(uint32_t* word, uint32_t bits) {
+  const unsigned m = __reduce_max_sync(0xffffffffu, bits);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(word, m);
+}
+
 // Per-precision hooks of the generic cell code.
 struct F32Form {
   using T = float;
@@ -144,19 +172,28 @@ __device__ __forceinline__ void window_after_step(const JobIO& J, const Policy& 
 // or Bateman form, window slide, stores.  Returns true (and stores nothing)
 // if the cell goes to the FP64 queue.
 // ---------------------------------------------------------------------------
+// With `change` set (ION_CONSERVATION_CHECK), *change receives
+// |sum_r v'_r - sum_r v_r| over the window, 0 if the cell is queued.
 template <typename T, int WM>
 __device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, int c, int lo,
                                             int hi, T (&v)[WM], const T (&lam)[WM],
-                                            bool allow_fb) {
+                                            bool allow_fb, T* change = nullptr) {
   T* __restrict__ N = static_cast<T*>(J.N);
   const int w = hi - lo + 1;
   T dne = T(0);
   int nlo = lo, nhi = hi;
+  if (change) *change = T(0);
   if constexpr (WM >= 2) {
     if (w >= 2) {
       T lmax = T(0);
 #pragma unroll
       for (int r = 0; r < WM; ++r) lmax = fmax(lmax, lam[r]);
+      ExactSum<T> acc;
+      if (change) {
+#pragma unroll
+        for (int r = 0; r < WM; ++r)
+          if (r < w) acc.add(-v[r]);
+      }
       if (lmax <= DDParams<T>::prop_max) {
         dne = taylor_propagate<T, WM>(v, lam, w, lmax);
       } else {
@@ -165,6 +202,12 @@ __device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, i
              (pol.gap > 0.0 && near_degenerate<T, WM>(lam, w, pol_gap<T>(pol)))))
           return true;
         dne = dd_update<T, WM>(v, lam, w);
+      }
+      if (change) {
+#pragma unroll
+        for (int r = 0; r < WM; ++r)
+          if (r < w) acc.add(v[r]);
+        *change = fabs(acc.value());
       }
       window_after_step<T, WM>(J, pol, v, w, nlo, nhi);
       T* p = N + (int64_t)lo * J.ld + c;
@@ -190,7 +233,8 @@ template <class F, int WM>
 __device__ __forceinline__ bool finish_cell(const JobIO& J, const Policy& pol,
                                             const typename F::Staged& tab, int c,
                                             typename F::T Ec, int lo, int hi,
-                                            typename F::T (&v)[WM], bool allow_fb) {
+                                            typename F::T (&v)[WM], bool allow_fb,
+                                            typename F::T* change = nullptr) {
   using T = typename F::T;
   const int w = hi - lo + 1;
   T lam[WM];
@@ -202,7 +246,7 @@ __device__ __forceinline__ bool finish_cell(const JobIO& J, const Policy& pol,
     for (int r = 0; r < WM; ++r)
       if (r < w - 1) lam[r] = F::rate(tab, lo + r, f);
   }
-  return update_cell<T, WM>(J, pol, c, lo, hi, v, lam, allow_fb);
+  return update_cell<T, WM>(J, pol, c, lo, hi, v, lam, allow_fb, change);
 }
 
 // The same, loading the window from global memory; W bounds the width.
@@ -210,7 +254,7 @@ template <class F, int W>
 __device__ __forceinline__ bool global_cell(const JobIO& J, const Policy& pol,
                                             const typename F::Staged& tab, int c,
                                             typename F::T Ec, int lo, int hi,
-                                            bool allow_fb) {
+                                            bool allow_fb, typename F::T* change = nullptr) {
   using T = typename F::T;
   const T* __restrict__ N = static_cast<const T*>(J.N);
   T v[W];
@@ -220,7 +264,7 @@ __device__ __forceinline__ bool global_cell(const JobIO& J, const Policy& pol,
     v[r] = r < hi - lo + 1 ? __ldcs(p) : T(0);
     p += J.ld;
   }
-  return finish_cell<F, W>(J, pol, tab, c, Ec, lo, hi, v, allow_fb);
+  return finish_cell<F, W>(J, pol, tab, c, Ec, lo, hi, v, allow_fb, change);
 }
 
 }  // namespace ion

@@ -551,12 +551,15 @@ __device__ __forceinline__ T dd_update(T (&v)[WM], const T (&lam)[WM], int w) {
   // Rates that fall along the window (the usual ladder near threshold: each
   // state harder to ionize than the one below) or rise along it (far above
   // the barrier, where Eq. 1 grows with the charge) give monotone nodes and
-  // the short table; others take every subset.
+  // the short table; others take every subset.  Only the window's own w-1
+  // nodes are compared, so that the result does not depend on the bound WM.
   bool up = true, down = true;
 #pragma unroll
   for (int r = 0; r + 1 < NR; ++r) {
-    up = up && z[r] <= z[r + 1];
-    down = down && z[r] >= z[r + 1];
+    if (r + 1 < w - 1) {
+      up = up && z[r] <= z[r + 1];
+      down = down && z[r] >= z[r + 1];
+    }
   }
   const bool sorted = up || down;
   T D[1 << NR];

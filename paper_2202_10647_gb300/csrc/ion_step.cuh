@@ -18,12 +18,15 @@ constexpr int kHdrPlain = 4;     // surrogate step: cells that took the rates of
 constexpr int kHdrTimeout = 5;   // surrogate step: non-zero if a bounded wait gave up
 constexpr int kHdrRecNarrow = 6; // records of windows of <= kRecNarrow states (from the front)
 constexpr int kHdrRecWide = 7;   // records of wider windows (from the back of the arrays)
-constexpr int kHdrChunk = 8;     // streaming kernel: next chunk to hand out
-constexpr int kHdrWords = 9;
+constexpr int kHdrChunk = 8;     // streaming kernels: next chunk or group to hand out
+constexpr int kHdrHot = 9;       // (reserved)
+constexpr int kHdrCons = 10;     // ION_CONSERVATION_CHECK: largest |change of sum_k N_k|
+constexpr int kHdrWords = 11;
 // Records of at most this many window states take the short divided-difference
 // table (3 rates, 7 subsets); wider ones the long one (5 rates, 31 subsets).
 constexpr int kRecNarrow = 4;
 constexpr size_t kHdrBytes = 256;
+static_assert(kHdrWords * 4 <= (int)kHdrBytes, "the header words fit the header");
 
 // Largest number of species one batched launch advances.
 constexpr int kMaxJobs = 8;
@@ -94,7 +97,7 @@ struct Scratch {
 
 struct BatchArgs {
   int njobs;
-  int nchunks;  // full chunks over all jobs
+  int nchunks;  // full chunks over all jobs (queue form: groups)
   JobIO job[kMaxJobs];
   Policy pol;
   Scratch ws;

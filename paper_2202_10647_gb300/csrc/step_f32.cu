@@ -144,12 +144,16 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 template <int Q>
 using PlaneRows = typename VecOf<Q>::T[ION_MAX_WINDOW][32];
 
-template <int Q, int WM, bool AD>
+// CONS (the call has ION_CONSERVATION_CHECK; a separate instantiation, so
+// that the other calls carry none of it): cmax becomes the larger of itself
+// and the bits of |sum_r v'_r - sum_r v_r| of each cell finished here.
+template <int Q, int WM, bool AD, bool CONS>
 __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
                                            const StagedF32& tab, const PlaneRows<Q>& P,
                                            int lane, int c0, const float (&Ev)[Q],
                                            const int (&lo)[Q], const int (&hi)[Q],
-                                           const bool (&ok)[Q], bool uni, bool (&stiff)[Q], float thr_lane) {
+                                           const bool (&ok)[Q], bool uni, bool (&stiff)[Q],
+                                           float thr_lane, uint32_t& cmax) {
   int w[Q];
   float v[Q][WM];
 #pragma unroll
@@ -246,6 +250,17 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     }
 #pragma unroll
     for (int r = 0; r < WM; ++r) v[j][r] += inc[j][r];
+    if constexpr (CONS) {
+      ExactSum<float> acc;
+#pragma unroll
+      for (int r = 0; r < WM; ++r) {
+        if (r < w[j]) {
+          acc.add(-vget(P[r][lane], j));
+          acc.add(v[j][r]);
+        }
+      }
+      cmax = max(cmax, abs_bits(acc.value()));
+    }
     if ((pol.flags & ION_NO_WINDOW_UPDATE) == 0) {
       if constexpr (AD)
         adapt_window<float, WM>(v[j], w[j], J.Z, pol.eps_f, pol.wmin, pol.wmax,
@@ -355,7 +370,7 @@ __device__ __forceinline__ void tail_records(const BatchArgs& a, int kChunk, int
 
 // AD: the adaptive window policy (a separate instantiation, so that the
 // fixed rule's kernels carry none of it).
-template <int Q, int W, bool AD>
+template <int Q, int W, bool AD, bool CONS>
 __global__ void __maxnreg__(stream_regs<Q>())
     ion_stream_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -465,6 +480,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
   };
 
   const float thr_lane = lane < kEasyTerms ? kThrF32[lane] : __int_as_float(0x7f800000);
+  uint32_t cmax = 0;  // largest |change of sum_k N_k| (bits), ION_CONSERVATION_CHECK
   // Chunk k lives in stage k mod 4.  Commit groups go out in the order
   // front(k+3), planes(k+2) in iteration k, so one wait that leaves the two
   // newest pending (planes(k+1), front(k+3)) completes front(k+2) and
@@ -571,11 +587,14 @@ __global__ void __maxnreg__(stream_regs<Q>())
         }
       }
     } else if (WMw == 2) {
-      easy_cells<Q, 2, AD>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
+      easy_cells<Q, 2, AD, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
+                                     thr_lane, cmax);
     } else if (WMw <= 4) {
-      easy_cells<Q, 4, AD>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
+      easy_cells<Q, 4, AD, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
+                                     thr_lane, cmax);
     } else {
-      easy_cells<Q, 6, AD>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff, thr_lane);
+      easy_cells<Q, 6, AD, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
+                                     thr_lane, cmax);
     }
     // stiff cells: their inputs (as loaded) go to the record queue
     bool any = false;
@@ -593,6 +612,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
     __syncwarp();
   }
   cp_async_wait<0>();
+  if constexpr (CONS) warp_max_into(&a.ws.hdr[kHdrCons], cmax);
 
   tail_records(a, kChunk, gw, TW, lane);
 }
@@ -632,7 +652,7 @@ constexpr size_t lean_smem() {
   return sizeof(StagedF32) + (size_t)W * kStages * sizeof(LStage<Q>);
 }
 
-template <int Q, int W>
+template <int Q, int W, bool CONS>
 __global__ void __maxnreg__(stream_regs<Q>())
     ion_lean_kernel(const __grid_constant__ BatchArgs a) {
   static_assert(Q == 1 || Q == 2, "one 16-byte front copy per lane at most");
@@ -719,12 +739,16 @@ __global__ void __maxnreg__(stream_regs<Q>())
       const uint32_t c0 = g * (uint32_t)kChunk + (uint32_t)(Q * lane);
       const uint32_t pd = s_base + s * kStageBytes + p_dst;
       if (bytes_equal<Q>(l) && bytes_equal<Q>(h)) {
-        const int rows = cold ? min(w[0], 1) : w[0];
         uint32_t off = (uint32_t)lo[0] * ld + c0;
+        if (cold) {
+          // the lowest plane alone (the window rule's)
+          if (w[0] >= 1) cp_async_s<4 * Q>(pd, Nf + off);
+        } else {
 #pragma unroll
-        for (int r = 0; r < ION_MAX_WINDOW; ++r) {
-          if (r < rows) cp_async_s<4 * Q>(pd + r * 32 * (uint32_t)sizeof(V), Nf + off);
-          off += ld;
+          for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+            if (r < w[0]) cp_async_s<4 * Q>(pd + r * 32 * (uint32_t)sizeof(V), Nf + off);
+            off += ld;
+          }
         }
       } else {
 #pragma unroll
@@ -742,6 +766,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
   };
 
   const float thr_lane = lane < kEasyTerms ? kThrF32[lane] : __int_as_float(0x7f800000);
+  uint32_t cmax = 0;  // largest |change of sum_k N_k| (bits), ION_CONSERVATION_CHECK
   // Chunk k lives in stage k mod 4, and the wait discipline is that of
   // ion_stream_kernel: fronts three chunks ahead, planes two.
   uint32_t run_next = fetch_run();
@@ -840,14 +865,14 @@ __global__ void __maxnreg__(stream_regs<Q>())
     } else {
       const int WMw = __reduce_max_sync(kFull, wl);
       if (WMw <= 2)
-        easy_cells<Q, 2, false>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
-                                thr_lane);
+        easy_cells<Q, 2, false, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni,
+                                       stiff, thr_lane, cmax);
       else if (WMw <= 4)
-        easy_cells<Q, 4, false>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
-                                thr_lane);
+        easy_cells<Q, 4, false, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni,
+                                       stiff, thr_lane, cmax);
       else
-        easy_cells<Q, 6, false>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni, stiff,
-                                thr_lane);
+        easy_cells<Q, 6, false, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni,
+                                       stiff, thr_lane, cmax);
       // stiff cells: their inputs (as loaded) go to the record queue
       bool any = false;
 #pragma unroll
@@ -865,6 +890,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
     __syncwarp();
   }
   cp_async_wait<0>();
+  if constexpr (CONS) warp_max_into(&a.ws.hdr[kHdrCons], cmax);
 
   tail_records(a, kChunk, gw, TW, lane);
 }
@@ -874,13 +900,13 @@ __global__ void __maxnreg__(stream_regs<Q>())
 template <int W>
 __device__ __forceinline__ bool record_cell(const BatchArgs& a, const StagedF32& tab,
                                             const JobIO& J, int64_t i, int c, float Ec,
-                                            int lo, int hi) {
+                                            int lo, int hi, float* change) {
   float v[W];
   const int w = hi - lo + 1;
 #pragma unroll
   for (int r = 0; r < W; ++r)
     v[r] = r < w ? __ldcs(a.ws.rec_V + (int64_t)r * a.ws.rec_cap + i) : 0.0f;
-  return finish_cell<F32Form, W>(J, a.pol, tab, c, Ec, lo, hi, v, true);
+  return finish_cell<F32Form, W>(J, a.pol, tab, c, Ec, lo, hi, v, true, change);
 }
 
 __global__ void __launch_bounds__(256)
@@ -898,6 +924,8 @@ __global__ void __launch_bounds__(256)
   if (blockIdx.x * blockDim.x >= n_up) return;  // no record for this block
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   __syncthreads();
+  const bool check = (a.pol.flags & ION_CONSERVATION_CHECK) != 0;
+  uint32_t cmax = 0;  // largest |change of sum_k N_k| (bits)
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n_up; t += stride) {
     const bool wide = t >= nn_up;  // warp-uniform
     const unsigned i = wide ? (unsigned)a.ws.rec_cap - 1u - (t - nn_up) : t;
@@ -923,27 +951,33 @@ __global__ void __launch_bounds__(256)
       // (a bound of 5 for warps of 5-state windows measured slower: the
       // extra instantiation costs more than its shorter table saves)
       static_assert(kRecNarrow == 4, "width bounds of the two record classes");
+      float d = 0.0f;
+      float* dp = check ? &d : nullptr;
       if (wide) {
-        fb = record_cell<6>(a, tab, J, i, c, Ec, lo, hi);
+        fb = record_cell<6>(a, tab, J, i, c, Ec, lo, hi, dp);
       } else if (wl == 1) {
-        fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi);
+        fb = record_cell<1>(a, tab, J, i, c, Ec, lo, hi, dp);
       } else if (Wm <= 2) {
-        fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi);
+        fb = record_cell<2>(a, tab, J, i, c, Ec, lo, hi, dp);
       } else {
-        fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi);
+        fb = record_cell<4>(a, tab, J, i, c, Ec, lo, hi, dp);
       }
+      cmax = max(cmax, abs_bits(d));
     }
     warp_append(&a.ws.hdr[kHdrFallback], a.ws.queue, a.ws.queue_job, fb, (uint32_t)c,
                 (uint8_t)jid);
   }
+  if (check) warp_max_into(&a.ws.hdr[kHdrCons], cmax);
 }
 
 // ---------------------------------------------------------------------------
 // FP64-coefficient pass over the queued cells, one cell per thread.
 // ---------------------------------------------------------------------------
+// Returns, with ION_CONSERVATION_CHECK, |sum_r v'_r - sum_r v_r| of the
+// window as stored (the inputs summed in FP64 exactly enough: w <= 6 floats).
 template <int W>
-__device__ __forceinline__ void fb_cell(const JobIO& J, const Policy& pol,
-                                        const StagedF32& tab, int c, int lo, int hi) {
+__device__ __forceinline__ float fb_cell(const JobIO& J, const Policy& pol,
+                                         const StagedF32& tab, int c, int lo, int hi) {
   float* __restrict__ N = static_cast<float*>(J.N);
   const FieldF32 f = field_f32(static_cast<const float*>(J.E)[c]);
   double v[W], lam[W];
@@ -952,12 +986,17 @@ __device__ __forceinline__ void fb_cell(const JobIO& J, const Policy& pol,
     v[r] = (double)N[(int64_t)(lo + r) * J.ld + c];
     lam[r] = (r < W - 1 && !pol.zero_dt) ? (double)rate_dt_f32(tab, lo + r, f) : 0.0;
   }
+  double s0 = 0.0;
+#pragma unroll
+  for (int r = 0; r < W; ++r) s0 += v[r];
   const double dne = dd_update<double, W>(v, lam, W);
   float vf[W];
+  double s1 = 0.0;
 #pragma unroll
   for (int r = 0; r < W; ++r) {
     vf[r] = __double2float_rn(v[r]);
     N[(int64_t)(lo + r) * J.ld + c] = vf[r];
+    s1 += (double)vf[r];
   }
   int nlo = lo, nhi = hi;
   window_after_step<float, W>(J, pol, vf, W, nlo, nhi);
@@ -966,6 +1005,7 @@ __device__ __forceinline__ void fb_cell(const JobIO& J, const Policy& pol,
   static_cast<float*>(J.dne)[c] = G ? d * G[c] : d;
   J.lo[c] = (uint8_t)nlo;
   J.hi[c] = (uint8_t)nhi;
+  return (float)fabs(s1 - s0);
 }
 
 __global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ BatchArgs a) {
@@ -974,6 +1014,7 @@ __global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ Bat
   if (blockIdx.x * blockDim.x >= n) return;  // no queued cell for this block
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   __syncthreads();
+  uint32_t cmax = 0;  // largest |change of sum_k N_k| (bits), ION_CONSERVATION_CHECK
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += gridDim.x * blockDim.x) {
     const int c = (int)a.ws.queue[i];
@@ -981,26 +1022,29 @@ __global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ Bat
     const JobIO& J = a.job[jid];
     const StagedF32& tab = tabs[jid];
     const int lo = J.lo[c], hi = J.hi[c];
+    float d = 0.0f;
     switch (hi - lo + 1) {
       case 2:
-        fb_cell<2>(J, a.pol, tab, c, lo, hi);
+        d = fb_cell<2>(J, a.pol, tab, c, lo, hi);
         break;
       case 3:
-        fb_cell<3>(J, a.pol, tab, c, lo, hi);
+        d = fb_cell<3>(J, a.pol, tab, c, lo, hi);
         break;
       case 4:
-        fb_cell<4>(J, a.pol, tab, c, lo, hi);
+        d = fb_cell<4>(J, a.pol, tab, c, lo, hi);
         break;
       case 5:
-        fb_cell<5>(J, a.pol, tab, c, lo, hi);
+        d = fb_cell<5>(J, a.pol, tab, c, lo, hi);
         break;
       case 6:
-        fb_cell<6>(J, a.pol, tab, c, lo, hi);
+        d = fb_cell<6>(J, a.pol, tab, c, lo, hi);
         break;
       default:
         break;
     }
+    cmax = max(cmax, abs_bits(d));
   }
+  if (a.pol.flags & ION_CONSERVATION_CHECK) warp_max_into(&a.ws.hdr[kHdrCons], cmax);
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,6 +1056,7 @@ struct StreamVariant {
   int Q, W;
   bool adaptive;
   bool lean;  // ion_lean_kernel (one species, the paper's window rule)
+  bool cons;  // ION_CONSERVATION_CHECK
   size_t (*smem)(int);
 };
 
@@ -1025,24 +1070,36 @@ size_t lean_smem_of(int) {
   return lean_smem<Q, W>();
 }
 
-#define ION_VARIANT(Q, W, AD) \
-  { reinterpret_cast<const void*>(&ion_stream_kernel<Q, W, AD>), Q, W, AD, false, &smem_of<Q, W> }
-#define ION_VARIANTS(AD)                                                          \
-  ION_VARIANT(1, 2, AD), ION_VARIANT(1, 4, AD), ION_VARIANT(1, 8, AD),             \
-      ION_VARIANT(2, 2, AD), ION_VARIANT(2, 4, AD), ION_VARIANT(2, 8, AD),         \
-      ION_VARIANT(4, 2, AD), ION_VARIANT(4, 4, AD), ION_VARIANT(4, 8, AD)
-#define ION_LEAN(Q, W) \
-  { reinterpret_cast<const void*>(&ion_lean_kernel<Q, W>), Q, W, false, true, &lean_smem_of<Q, W> }
-const StreamVariant kVariants[] = {ION_VARIANTS(false), ION_VARIANTS(true),
-                                   ION_LEAN(1, 2), ION_LEAN(1, 4), ION_LEAN(1, 8),
-                                   ION_LEAN(2, 2), ION_LEAN(2, 4), ION_LEAN(2, 8)};
+#define ION_VARIANT(Q, W, AD, C)                                                     \
+  {                                                                                  \
+    reinterpret_cast<const void*>(&ion_stream_kernel<Q, W, AD, C>), Q, W, AD, false, C, \
+        &smem_of<Q, W>                                                               \
+  }
+#define ION_VARIANTS(AD, C)                                                       \
+  ION_VARIANT(1, 2, AD, C), ION_VARIANT(1, 4, AD, C), ION_VARIANT(1, 8, AD, C),    \
+      ION_VARIANT(2, 2, AD, C), ION_VARIANT(2, 4, AD, C), ION_VARIANT(2, 8, AD, C), \
+      ION_VARIANT(4, 2, AD, C), ION_VARIANT(4, 4, AD, C), ION_VARIANT(4, 8, AD, C)
+#define ION_LEAN(Q, W, C)                                                              \
+  {                                                                                    \
+    reinterpret_cast<const void*>(&ion_lean_kernel<Q, W, C>), Q, W, false, true, C,      \
+        &lean_smem_of<Q, W>                                                            \
+  }
+#define ION_LEANS(C)                                                              \
+  ION_LEAN(1, 2, C), ION_LEAN(1, 4, C), ION_LEAN(1, 8, C), ION_LEAN(2, 2, C),      \
+      ION_LEAN(2, 4, C), ION_LEAN(2, 8, C)
+const StreamVariant kVariants[] = {ION_VARIANTS(false, false), ION_VARIANTS(true, false),
+                                   ION_VARIANTS(false, true),  ION_VARIANTS(true, true),
+                                   ION_LEANS(false),           ION_LEANS(true)};
+#undef ION_LEANS
 #undef ION_LEAN
 #undef ION_VARIANTS
 #undef ION_VARIANT
 
-const StreamVariant* find_variant(int Q, int W, bool adaptive = false, bool lean = false) {
+const StreamVariant* find_variant(int Q, int W, bool adaptive = false, bool lean = false,
+                                  bool cons = false) {
   for (const auto& v : kVariants)
-    if (v.Q == Q && v.W == W && v.adaptive == adaptive && v.lean == lean) return &v;
+    if (v.Q == Q && v.W == W && v.adaptive == adaptive && v.lean == lean && v.cons == cons)
+      return &v;
   return nullptr;
 }
 
@@ -1130,7 +1187,8 @@ cudaError_t launch_batch_f32(BatchArgs& a, const LaunchShape& shape, int num_sms
                              cudaStream_t s) {
   const StreamVariant* v =
       find_variant(shape.cells_per_lane, shape.warps_per_block, a.pol.adaptive != 0,
-                   lean_fits(a, shape.cells_per_lane));
+                   lean_fits(a, shape.cells_per_lane),
+                   (a.pol.flags & ION_CONSERVATION_CHECK) != 0);
   if (!v) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.ws.hdr, 0, kHdrWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;

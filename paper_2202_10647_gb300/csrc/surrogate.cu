@@ -52,6 +52,7 @@ struct Consts {
   float bin_a, bin_b;  // bin = floor(bin_a log2|E| + bin_b)
   int nbins;
   int Z, KP;
+  int dead_wait;  // test hook (ion_surrogate_test_timeout): see mbar_wait below
 };
 
 // Device image of a surrogate (one allocation).
@@ -115,9 +116,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-// Bounded wait for the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+// Bounded wait for the mbarrier phase with the given parity: false if the
+// phase has not completed after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint32_t limit = kSpinLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -171,7 +174,7 @@ __host__ __device__ constexpr Plan plan_of(int KP) {
   p.consts = p.w3 + (uint32_t)KP * 128;
   p.tab = p.consts + (uint32_t)((sizeof(Consts) + 15) / 16 * 16);
   p.bar = p.tab + (uint32_t)((sizeof(StagedF32) + 15) / 16 * 16);
-  p.slot = p.bar + 8;
+  p.slot = p.bar + 16;  // two barriers: the MMA commits', and one never arrived at
   p.total = p.slot + 8 + 1024;  // + slack for aligning the base to 1024
   return p;
 }
@@ -256,6 +259,8 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1)
                  : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + 1)), "r"(1)
+                 : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -273,6 +278,12 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
   const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
   const uint32_t sA = smem_u32(A), sW2 = smem_u32(base + P.w2), sW3 = smem_u32(base + P.w3);
   const uint32_t sbar = smem_u32(bar);
+  // Test hook: the first wait of a tile polls, 64 times, a second barrier
+  // that nothing arrives at, so that it gives up while the layer-2 MMAs are
+  // in flight and the timeout path below runs (the drain at the end then
+  // waits, with the full limit, for the commit it skipped).
+  const uint32_t sdead = smem_u32(bar + 1);
+  const bool dead_wait = K.dead_wait != 0;
   const int Z = K.Z;
   const float log2dt = (float)a.pol.log2dt;
   unsigned char* row = A + (t >> 3) * 1024 + (t & 7) * 128;
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
                  kk > 0 ? 1u : 0u);
       mma_commit(sbar);
     }
-    bool ok = mbar_wait(sbar, phase);
+    bool ok = dead_wait ? mbar_wait(sdead, 0u, 64u) : mbar_wait(sbar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
       failed = true;
@@ -688,6 +699,18 @@ int ion_surrogate_create(const ion_species* sp, const float* P, const ion_surrog
   }
   *out = s;
   return set_error(ION_OK, "%s", "");
+}
+
+int ion_surrogate_test_timeout(ion_surrogate* s, int on) {
+  const int rc = check_surrogate(s);
+  if (rc) return rc;
+  const int v = on ? 1 : 0;
+  const cudaError_t e = cudaMemcpy(reinterpret_cast<char*>(s->dev) + offsetof(Dev, k) +
+                                       offsetof(ion::sg::Consts, dead_wait),
+                                   &v, sizeof v, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess)
+    return ion::set_error(ION_ECUDA, "ion_surrogate_test_timeout: %s", cudaGetErrorString(e));
+  return ion::set_error(ION_OK, "%s", "");
 }
 
 int ion_surrogate_destroy(ion_surrogate* s) {

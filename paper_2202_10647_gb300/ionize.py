@@ -26,6 +26,7 @@ ION_F64_PLAIN = 0x1
 ION_NO_WINDOW_UPDATE = 0x2
 ION_NO_FP64_FALLBACK = 0x4
 ION_FORCE_FP64_COEF = 0x8
+ION_CONSERVATION_CHECK = 0x10
 
 ION_DTYPE_F32 = 0
 ION_DTYPE_F64 = 1
@@ -40,7 +41,8 @@ EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
            "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
            "ion_surrogate_create", "ion_surrogate_destroy", "ion_surrogate_rates",
-           "ion_step_surrogate", "ion_measure_peaks", "ion_binary_version",
+           "ion_step_surrogate", "ion_surrogate_test_timeout", "ion_measure_peaks",
+           "ion_binary_version",
            "ion_last_error")
 
 #: forward pass in the tensor-core arithmetic (bf16 W2, W3, h1, h2; SFU tanh)
@@ -183,6 +185,8 @@ def _declare(lib):
     lib.ion_step_surrogate.argtypes = [_vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp, _vp,
                                        _vp, _vp, ctypes.POINTER(_StepOpts), ctypes.c_double,
                                        _vp, ctypes.c_size_t, _vp]
+    lib.ion_surrogate_test_timeout.restype = ctypes.c_int
+    lib.ion_surrogate_test_timeout.argtypes = [_vp, ctypes.c_int]
     lib.ion_measure_peaks.restype = ctypes.c_int
     lib.ion_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.ion_binary_version.restype = ctypes.c_int
@@ -458,6 +462,20 @@ def stiff_cells(ws: torch.Tensor) -> int:
     return int(ws[8:12].cpu().view(torch.int32)[0])
 
 
+def changing_cells(ws: torch.Tensor) -> int:
+    """Cells of the last FP32 step under the paper's window rule (16-byte
+    aligned |E|, k_lo, k_hi) that some window rate could change: the others
+    have every window rate below W dt = 2^-30 and keep their populations;
+    synchronizes."""
+    return int(ws[36:40].cpu().view(torch.int32)[0])
+
+
+def conservation_change(ws: torch.Tensor) -> float:
+    """With ION_CONSERVATION_CHECK: the largest |sum_k N'_k - sum_k N_k| over
+    the cells of the last step that used `ws` (synchronizes)."""
+    return float(ws[40:44].cpu().view(torch.float32)[0])
+
+
 def conservation(N: torch.Tensor, out: torch.Tensor, ncells: int | None = None,
                  nplanes: int | None = None, target: float = 1.0) -> torch.Tensor:
     """ion_conservation: writes max_c |sum_k N[k, c] - target| over the
@@ -583,6 +601,11 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+    def test_timeout(self, on: bool = True) -> None:
+        """ion_surrogate_test_timeout: make the kernels' first tensor-core
+        wait give up (on) or wait normally (off)."""
+        _check(lib().ion_surrogate_test_timeout(self._h, int(bool(on))))
 
     def rates(self, E: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """W_k(|E|) in 1/fs from the network, (Z, ncells)."""

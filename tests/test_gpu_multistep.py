@@ -176,3 +176,74 @@ def test_krypton_full_size_sampled():
           f"steps of {idx.size} cells; cumulative drift from t = 0: step 1 {drift[0]:.2e}, "
           f"step 50 {drift[-1]:.2e} ({int(ref[-1][4].sum())} cells left out); max |sum N - 1| "
           f"after step 1 {float(cons[0]):.2e}, after 50 {float(cons[-1]):.2e}")
+
+
+@pytest.mark.parametrize("case", ["nitrogen_3d", "Ar-like", "Ar-like adaptive", "nitrogen FP64"])
+def test_step_conservation_measure(case):
+    """ION_CONSERVATION_CHECK: the step's own measure, the largest change of
+    a cell's total population max_c |sum_k N'_k - sum_k N_k|, equals the same
+    quantity computed on the host in FP64 from the populations before and
+    after the step (every kernel of the step contributes: the streaming or
+    single-species kernel, the records, the FP64-coefficient queue)."""
+    dev = "cuda"
+    window = None
+    flags = ionize.ION_CONSERVATION_CHECK
+    if case.startswith("nitrogen"):
+        wl = W.nitrogen_3d(8, 32, 64, seed=51)
+    else:
+        wl = W.ladder_cells(W.argon_like(), 30011, 52, block=64)
+    if case.endswith("adaptive"):
+        window = dict(w_min=2, w_max=6, eps_grow=1e-6)
+    dt_ = torch.float32
+    if case.endswith("FP64"):
+        flags |= ionize.ION_F64_PLAIN
+        dt_ = torch.float64
+    n = wl.ncells
+    sp = gpu_species(wl.species)
+    E, N = wl.E.to(dt_).to(dev), wl.N.to(dt_).to(dev)
+    lo, hi = wl.lo.clone().to(dev), wl.hi.clone().to(dev)
+    dne = torch.zeros(n, dtype=dt_, device=dev)
+    N0 = N.clone()
+    ws = ionize.step(sp, E, N, lo, hi, 0.05, dne, flags=flags, window=window)
+    torch.cuda.synchronize()
+    got = ionize.conservation_change(ws)
+    want = float((N[:, :n].double().sum(0) - N0[:, :n].double().sum(0)).abs().max())
+    assert got == pytest.approx(want, rel=1e-5, abs=1e-15), (got, want)
+    assert 0.0 < got <= 1e-6 or dt_ == torch.float64
+    # without the flag the word stays 0, and the step is the same
+    N2, lo2, hi2 = N0.clone(), wl.lo.clone().to(dev), wl.hi.clone().to(dev)
+    dne2 = torch.zeros(n, dtype=dt_, device=dev)
+    ws2 = ionize.step(sp, E, N2, lo2, hi2, 0.05, dne2,
+                      flags=flags & ~ionize.ION_CONSERVATION_CHECK, window=window)
+    torch.cuda.synchronize()
+    assert ionize.conservation_change(ws2) == 0.0
+    assert torch.equal(N, N2) and torch.equal(lo, lo2) and torch.equal(hi, hi2)
+
+
+def test_graph_with_fused_conservation():
+    """The 50-step graph with the fused check: the populations are those of
+    the graph with the full check after every step, the fused measure of
+    step 1 equals the full check after step 1 (the run starts from
+    sum_k N_k = 1 exactly), and the full check after step 50 stays within
+    the sum of the 50 fused measures."""
+    wl, fields = small_krypton()
+    n = wl.ncells
+    sp = gpu_species(wl.species)
+    runs = {}
+    for mode in ("full", "fused"):
+        N, lo, hi = wl.N.clone(), wl.lo.clone(), wl.hi.clone()
+        dne = torch.zeros(n, device="cuda")
+        g = multistep.StepGraph(sp, fields, N, lo, hi, dne, DT, conservation=mode)
+        g.replay()
+        torch.cuda.synchronize()
+        runs[mode] = (N, lo, hi, dne, g)
+    Nf, lf, hf, df, gf = runs["full"]
+    Nu, lu, hu, du, gu = runs["fused"]
+    assert torch.equal(Nf, Nu) and torch.equal(lf, lu) and torch.equal(hf, hu)
+    assert torch.equal(df, du)
+    c, full = gu.cons.double().cpu().numpy(), gu.cons_full.double().cpu().numpy()
+    assert full[0] == pytest.approx(c[0], rel=1e-5, abs=1e-15)
+    assert full[0] == pytest.approx(float(gf.cons[0]), rel=1e-6, abs=1e-15)
+    assert full[1] == pytest.approx(float(gf.cons[-1]), rel=1e-6, abs=1e-15)
+    assert full[1] <= c.sum() * (1 + 1e-5) + 1e-12
+    assert np.all(c <= 1e-6)

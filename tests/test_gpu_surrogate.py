@@ -286,3 +286,51 @@ def test_full_size_surrogate_sampled(argon_net):
     assert float((wl.N[:, :n].double().sum(0) - tot0).abs().max()) <= 1e-6
     No, _, _, _ = oracle.step(oracle_species(sd), Es, Ns, 0.05, ls, hs)
     assert np.abs(wl.N[:, ix].double().cpu().numpy() - No).max() <= 2e-6
+
+
+def test_bounded_wait_gives_up_and_frees_tensor_memory():
+    """The surrogate kernels' bounded mbarrier wait, made to give up by the
+    test hook (the first wait of each tile polls a barrier nothing arrives
+    at): the step leaves every cell untouched and sets header word 5, the
+    rates kernel writes NaN, and each CTA still waits for the matrix
+    products it skipped and frees its tensor memory, so that the next normal
+    calls run and give the plain step's result."""
+    sd = W.argon_like()
+    sp = gpu_species(sd)
+    P = torch.tensor(rand_P(sd.Z, 11, 0.3), dtype=torch.float32, device="cuda")
+    l2lo, l2hi = S.log2_range()
+    norm = {"log2E_min": l2lo, "log2E_max": l2hi, "y_floor": -40.0,
+            "y_mean": [0.0] * sd.Z, "y_scale": [1.0] * sd.Z}
+    net = ionize.Surrogate(sp, P, norm)
+    wl = W.ladder_cells(sd, 50000, 25)
+    n = wl.ncells
+    E = wl.E.cuda()
+    net.test_timeout(True)
+    try:
+        for rep in range(2):
+            N, lo, hi = wl.N.cuda(), wl.lo.clone().cuda(), wl.hi.clone().cuda()
+            dne = torch.full((n,), 5.0, device="cuda")
+            ws = net.step(E, N, lo, hi, 0.05, dne, pop_tol=1.0)
+            torch.cuda.synchronize()
+            n_net, n_plain, timeout = ionize.surrogate_counters(ws)
+            assert timeout > 0 and n_net == 0
+            assert torch.equal(N.cpu(), wl.N) and torch.equal(lo.cpu(), wl.lo)
+            assert torch.equal(hi.cpu(), wl.hi) and bool(torch.all(dne == 5.0))
+            Wn = net.rates(E[:4096].contiguous())
+            torch.cuda.synchronize()
+            assert bool(torch.isnan(Wn).all())
+    finally:
+        net.test_timeout(False)
+    # normal calls afterwards: tensor memory was freed, the network runs
+    N, lo, hi = wl.N.cuda(), wl.lo.clone().cuda(), wl.hi.clone().cuda()
+    dne = torch.zeros(n, device="cuda")
+    ws = net.step(E, N, lo, hi, 0.05, dne, pop_tol=0.0)
+    Wn = net.rates(E[:4096].contiguous())
+    N2, lo2, hi2 = wl.N.cuda(), wl.lo.clone().cuda(), wl.hi.clone().cuda()
+    dne2 = torch.zeros(n, device="cuda")
+    ionize.step(sp, E, N2, lo2, hi2, 0.05, dne2)
+    torch.cuda.synchronize()
+    assert ionize.surrogate_counters(ws)[2] == 0
+    assert bool(torch.isfinite(Wn).all())
+    assert float((N - N2).abs().max()) <= 2e-6
+    assert torch.equal(lo, lo2) and torch.equal(hi, hi2)
