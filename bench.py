@@ -782,7 +782,7 @@ def main():
                    "form": "FP32 + FP64 coefficients for |W_i-W_j| < 1e-3 max(W_i,W_j)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "kernel": "ion_step (ion_stream_kernel + ion_stiff_kernel + ion_fb_kernel)",
+                     "kernel": "ion_step (ion_lean_kernel + ion_stiff_kernel + ion_fb_kernel)",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": main_ms},
         "forms": {
