@@ -279,18 +279,21 @@ __device__ __forceinline__ double rate_dt_f64(const StagedF64& t, int k, double 
 // four levels); written as a divided difference it stays defined and
 // accurate for equal and nearly equal rates.
 //
-// dd_exp_all fills D[mask] = exp[{z_k : bit k of mask}] for every non-empty
-// subset, smallest subsets first:
-//   * spread s = max z - min z of the subset >= TAU: the two-term recurrence
-//     that removes the subset's smallest and its largest node,
-//       D(S) = (D(S \ {argmin}) - D(S \ {argmax})) / s.
-//     Dividing by the full spread bounds the cancellation (both terms are
-//     positive and the divisor is the largest gap in S).
-//   * s < TAU: the Taylor series of the divided difference about the
-//     largest node z*,
-//       exp[S] = e^{z*} sum_{r>=0} h_r(z - z*) / (|S|-1+r)!,
+// dd_exp_ranges fills D[j..i] = exp[z_j, ..., z_i] for every contiguous
+// range of nodes, shortest ranges first:
+//   * spread s = max z - min z of the range >= TAU: the two-term recurrence
+//     that removes one end of the range,
+//       D[j..i] = (D[j+1..i] - D[j..i-1]) / (z_i - z_j).
+//     When the ends are the range's smallest and largest nodes the divisor
+//     is its spread, which bounds the cancellation (both terms are positive);
+//     a range whose ends are close while an inner node lies far off is
+//     instead evaluated on its nodes in increasing order (dd_set).
+//   * s < TAU: the Taylor series of the divided difference about a node c
+//     of the range,
+//       exp[S] = e^{c} sum_{r>=0} h_r(z - c) / (|S|-1+r)!,
 //     h_r the complete homogeneous symmetric polynomial of degree r,
-//     truncated at the first R with s^(R+1)/(R+1)! below the target.
+//     truncated at the first R with s^(R+1)/(R+1)! below the target (FP64)
+//     or at the R that TAU itself needs (FP32).
 // ---------------------------------------------------------------------------
 // Number of Taylor terms: the smallest R with x^(R+1)/(R+1)! below the
 // target (3e-9 in FP32, 2e-17 in FP64), i.e. the number of thresholds
@@ -327,6 +330,8 @@ struct DDParams<float> {
   static constexpr int RMAX = 11;      // terms needed at spread tau
   static constexpr float prop_max = 1.0f;  // Taylor propagation up to max W dt
   static constexpr int PMAX = 16;      // terms needed at 2 * prop_max
+  static constexpr bool kUniform = true;  // every Taylor term up to RMAX
+  static constexpr float end_ratio = 8.0f;  // dd_exp_ranges' recurrence bound
   __device__ static __forceinline__ int terms(float x, int rmax) {
     int R = 0;
 #pragma unroll
@@ -344,6 +349,8 @@ struct DDParams<double> {
   static constexpr int RMAX = 12;
   static constexpr double prop_max = 0.5;
   static constexpr int PMAX = 18;
+  static constexpr bool kUniform = false;  // terms(s) of them
+  static constexpr double end_ratio = 8.0;
   __device__ static __forceinline__ int terms(double x, int rmax) {
     int R = 0;
 #pragma unroll
@@ -355,14 +362,6 @@ struct DDParams<double> {
   __device__ static __forceinline__ double inv_fact(int n) { return kInvFact[n]; }
 };
 
-__host__ __device__ constexpr int popc_c(int x) {
-  return x == 0 ? 0 : (x & 1) + popc_c(x >> 1);
-}
-
-__host__ __device__ constexpr int ctz_c(int x) {
-  return (x & 1) ? 0 : 1 + ctz_c(x >> 1);
-}
-
 // mask of the contiguous node range [j, i]
 __host__ __device__ constexpr int range_mask(int j, int i) {
   return ((1 << (i + 1)) - 1) & ~((1 << j) - 1);
@@ -370,118 +369,165 @@ __host__ __device__ constexpr int range_mask(int j, int i) {
 
 
 
-// Taylor branch of dd_exp_all for the subset `mask` of the nodes z[0..n-1]
-// (n <= 5), without the factor e^{zmx}: sum_r h_r(z - zmx) / (m-1+r)!.
-// Kept out of line: it is the rare branch, and one copy per precision keeps
-// the kernels small.
+// Taylor values of every contiguous range of nodes:
+// C[a][b] = sum_r h_r(z[a..b] - z[a]) / (b-a+r)!, the divided difference of
+// exp over z[a..b] without the factor e^{z[a]}.  The complete homogeneous
+// polynomials obey h_r(x_1..x_k) = h_r(x_1..x_{k-1}) + x_k h_{r-1}(x_1..x_k),
+// so one chain per left end a adds the nodes a+1, a+2, ... in turn and reads
+// off every range [a, b] on the way: NR(NR-1)/2 node additions for all the
+// ranges, instead of one series per range over its whole subset.  The series
+// is the same about any centre inside the range; about its first node the
+// offsets are at most the range's spread in size (either sign), which bounds
+// the terms as about the largest node.
+template <typename T, int NR>
+__device__ __forceinline__ void taylor_chains(const T (&z)[NR], int R, T (&C)[NR][NR]) {
+  using P = DDParams<T>;
+#pragma unroll
+  for (int a = 0; a + 1 < NR; ++a) {
+    T H[P::RMAX + 1];
+    H[0] = T(1);
+#pragma unroll
+    for (int r = 1; r <= P::RMAX; ++r) H[r] = T(0);
+#pragma unroll
+    for (int b = a + 1; b < NR; ++b) {
+      const T x = z[b] - z[a];
+#pragma unroll
+      for (int r = 1; r <= P::RMAX; ++r)
+        if (r <= R) H[r] = fma(x, H[r - 1], H[r]);
+      T acc = T(0);
+#pragma unroll
+      for (int r = P::RMAX; r >= 0; --r)  // smallest terms first
+        if (r <= R) acc = fma(H[r], P::inv_fact(b - a + r), acc);
+      C[a][b] = acc;
+    }
+  }
+}
+
 template <typename T>
-__device__ __noinline__ T dd_taylor(T z0, T z1, T z2, T z3, T z4, int mask,
-                                    T zmx, T s) {
-  using P = DDParams<T>;
-  const int R = P::terms(s, P::RMAX);
-  const T zz[5] = {z0, z1, z2, z3, z4};
-  T H[P::RMAX + 1];
-  H[0] = T(1);
-#pragma unroll
-  for (int r = 1; r <= P::RMAX; ++r) H[r] = T(0);
-  int m = 0;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    if (!((mask >> k) & 1)) continue;
-    ++m;
-    const T x = zz[k] - zmx;
-#pragma unroll
-    for (int r = 1; r <= P::RMAX; ++r)
-      if (r <= R) H[r] = fma(x, H[r - 1], H[r]);
-  }
-  T acc = T(0);
-#pragma unroll
-  for (int r = 0; r <= P::RMAX; ++r)
-    if (r <= R) acc = fma(H[r], P::inv_fact(m - 1 + r), acc);
-  return acc;
-}
+__device__ __noinline__ T dd_set(T z0, T z1, T z2, T z3, T z4, T e0, T e1, T e2, T e3, T e4,
+                                 int m);
 
+// The divided differences of exp over the contiguous ranges [j, i] that
+// dd_update reads, in any node order.  A range of spread below TAU takes its
+// Taylor value (taylor_chains); a wider one the recurrence that removes its
+// first or its last node, which stays on contiguous ranges (NR(NR-1)/2 of
+// them instead of the 2^NR - NR - 1 subsets of a recurrence that removes the
+// smallest and the largest node).  When the range's ends are its extremes
+// (rates falling or rising along the window) that is the same recurrence.
+// Otherwise the two terms can cancel: their relative difference is about
+// |z_i - z_j| / spread, so a live range (i < nlive; nodes past nlive are not
+// read by dd_update) whose spread exceeds END_RATIO |z_i - z_j| is evaluated
+// on its own nodes sorted (dd_set).
 template <typename T, int NR>
-__device__ __forceinline__ void dd_exp_all(const T (&z)[NR], const T (&ez)[NR],
-                                           T (&D)[1 << NR]) {
-  using P = DDParams<T>;
-  D[0] = T(0);
-#pragma unroll
-  for (int mask = 1; mask < (1 << NR); ++mask) {
-    if (popc_c(mask) == 1) {
-      D[mask] = ez[ctz_c(mask)];
-      continue;
-    }
-    T zmn = T(0), zmx = T(0), emx = T(0), dmin = T(0), dmax = T(0);
-    bool first = true;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (!((mask >> k) & 1)) continue;
-      const T zk = z[k];
-      const T dk = D[mask ^ (1 << k)];
-      if (first) {
-        zmn = zk;
-        zmx = zk;
-        emx = ez[k];
-        dmin = dk;
-        dmax = dk;
-        first = false;
-      } else {
-        const bool lo = zk < zmn, hi = zk > zmx;
-        zmn = lo ? zk : zmn;
-        dmin = lo ? dk : dmin;
-        zmx = hi ? zk : zmx;
-        emx = hi ? ez[k] : emx;
-        dmax = hi ? dk : dmax;
-      }
-    }
-    const T s = zmx - zmn;
-    T d;
-    if (s >= P::tau) {
-      d = P::div(dmin - dmax, s);
-    } else {
-      d = emx * dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
-                             NR > 2 ? z[NR > 2 ? 2 : 0] : T(0),
-                             NR > 3 ? z[NR > 3 ? 3 : 0] : T(0),
-                             NR > 4 ? z[NR > 4 ? 4 : 0] : T(0), mask, zmx, s);
-    }
-    D[mask] = d;
-  }
-}
-
-// The same for nodes in monotone order (z[0] <= ... <= z[NR-1] or the
-// reverse), and only the contiguous ranges [j, i] that dd_update reads: a
-// range's smallest and largest nodes are its ends, so dd_exp_all's
-// recurrence removes its first or its last node and stays on contiguous
-// ranges (NR(NR-1)/2 of them instead of 2^NR - NR - 1 subsets), dividing
-// by the same spread |z[i] - z[j]|.
-template <typename T, int NR>
-__device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR],
+__device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR], int nlive,
                                               T (&D)[1 << NR]) {
   using P = DDParams<T>;
 #pragma unroll
   for (int i = 0; i < NR; ++i) D[1 << i] = ez[i];
+  // spread of every range from running extremes
+  T S[NR][NR];
+  bool close = false;  // some live range has spread below TAU
+  T smax = T(0);       // the largest such spread
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    T mn = z[j], mx = z[j];
+#pragma unroll
+    for (int i = j + 1; i < NR; ++i) {
+      mn = fmin(mn, z[i]);
+      mx = fmax(mx, z[i]);
+      const T s = mx - mn;
+      S[j][i] = s;
+      if (i < nlive) {
+        close = close || s < P::tau;
+        smax = s < P::tau ? fmax(smax, s) : smax;
+      }
+    }
+  }
+  T C[NR][NR];
+#pragma unroll
+  for (int a = 0; a < NR; ++a)
+#pragma unroll
+    for (int b = 0; b < NR; ++b) C[a][b] = T(0);
+  if (close) taylor_chains<T, NR>(z, P::kUniform ? P::RMAX : P::terms(smax, P::RMAX), C);
 #pragma unroll
   for (int len = 2; len <= NR; ++len) {
 #pragma unroll
     for (int j = 0; j + len <= NR; ++j) {
       const int i = j + len - 1;
+      const T s = S[j][i];
       const T dz = z[i] - z[j];
-      const T s = fabs(dz);
       T d;
-      if (s >= P::tau) {
-        d = P::div(D[range_mask(j + 1, i)] - D[range_mask(j, i - 1)], dz);
+      if (s < P::tau) {
+        d = ez[j] * C[j][i];
+      } else if (len > 2 && i < nlive && s > P::end_ratio * fabs(dz)) {
+        // the range's own nodes, padded with z = 0 (the largest a node can be)
+        d = dd_set<T>(z[j], z[j + 1], z[j + 2 < NR ? j + 2 : j],
+                      len > 3 ? z[j + 3 < NR ? j + 3 : j] : T(0),
+                      len > 4 ? z[j + 4 < NR ? j + 4 : j] : T(0), ez[j], ez[j + 1],
+                      ez[j + 2 < NR ? j + 2 : j], len > 3 ? ez[j + 3 < NR ? j + 3 : j] : T(1),
+                      len > 4 ? ez[j + 4 < NR ? j + 4 : j] : T(1), len);
       } else {
-        const bool up = dz >= T(0);  // the largest node is the range's last
-        d = (up ? ez[i] : ez[j]) *
-            dd_taylor<T>(z[0], NR > 1 ? z[NR > 1 ? 1 : 0] : T(0),
-                         NR > 2 ? z[NR > 2 ? 2 : 0] : T(0), NR > 3 ? z[NR > 3 ? 3 : 0] : T(0),
-                         NR > 4 ? z[NR > 4 ? 4 : 0] : T(0), range_mask(j, i), up ? z[i] : z[j],
-                         s);
+        d = P::div(D[range_mask(j + 1, i)] - D[range_mask(j, i - 1)], dz);
       }
       D[range_mask(j, i)] = d;
     }
   }
+}
+
+// exp[z_0, ..., z_{m-1}] (3 <= m <= 5; the slots past m hold z = 0,
+// e^z = 1): the nodes sorted by a 9-comparator network, then the table of
+// their contiguous ranges level by level in place (d[j] = D[j..j+len-1]):
+// removing the smallest and the largest node, or the Taylor series about
+// the largest node below TAU.  Kept out of line and in loops: only ranges
+// with close ends and a far inner node come here.
+template <typename T>
+__device__ __noinline__ T dd_set(T z0, T z1, T z2, T z3, T z4, T e0, T e1, T e2, T e3, T e4,
+                                 int m) {
+  using P = DDParams<T>;
+  T z[5] = {z0, z1, z2, z3, z4};
+  T d[5] = {e0, e1, e2, e3, e4};
+  constexpr int kNet[9][2] = {{0, 1}, {3, 4}, {2, 4}, {2, 3}, {0, 3},
+                              {0, 2}, {1, 4}, {1, 3}, {1, 2}};
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const int p = kNet[c][0], q = kNet[c][1];
+    const bool sw = z[p] > z[q];
+    const T zp = z[p], dp = d[p];
+    z[p] = sw ? z[q] : zp;
+    d[p] = sw ? d[q] : dp;
+    z[q] = sw ? zp : z[q];
+    d[q] = sw ? dp : d[q];
+  }
+#pragma unroll 1
+  for (int len = 2; len <= m; ++len) {
+#pragma unroll 1
+    for (int j = 0; j + len <= m; ++j) {
+      const int i = j + len - 1;
+      const T zi = z[i], s = zi - z[j];
+      if (s >= P::tau) {
+        d[j] = P::div(d[j + 1] - d[j], s);
+      } else {
+        const int R = P::kUniform ? P::RMAX : P::terms(s, P::RMAX);
+        T H[P::RMAX + 1];
+        H[0] = T(1);
+#pragma unroll
+        for (int r = 1; r <= P::RMAX; ++r) H[r] = T(0);
+#pragma unroll 1
+        for (int k = j; k < i; ++k) {
+          const T x = z[k] - zi;
+#pragma unroll
+          for (int r = 1; r <= P::RMAX; ++r)
+            if (r <= R) H[r] = fma(x, H[r - 1], H[r]);
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int r = P::RMAX; r >= 0; --r)
+          if (r <= R) acc = fma(H[r], P::inv_fact(len - 1 + r), acc);
+        d[j] = exp(zi) * acc;
+      }
+    }
+  }
+  return d[0];
 }
 
 // Small rates: N' = sum_k (dt A)^k N / k! applied to the window vector
@@ -548,25 +594,13 @@ __device__ __forceinline__ T dd_update(T (&v)[WM], const T (&lam)[WM], int w) {
     z[r] = -l;
     ez[r] = exp(-l);
   }
-  // Rates that fall along the window (the usual ladder near threshold: each
-  // state harder to ionize than the one below) or rise along it (far above
-  // the barrier, where Eq. 1 grows with the charge) give monotone nodes and
-  // the short table; others take every subset.  Only the window's own w-1
-  // nodes are compared, so that the result does not depend on the bound WM.
-  bool up = true, down = true;
-#pragma unroll
-  for (int r = 0; r + 1 < NR; ++r) {
-    if (r + 1 < w - 1) {
-      up = up && z[r] <= z[r + 1];
-      down = down && z[r] >= z[r + 1];
-    }
-  }
-  const bool sorted = up || down;
+  // (Rates fall along the window in the usual ladder near threshold, each
+  // state harder to ionize than the one below, and rise far above the
+  // barrier, where Eq. 1 grows with the charge; both give ranges whose ends
+  // are their extremes.)  Only the window's own w-1 nodes are judged, so
+  // that the result does not depend on the bound WM.
   T D[1 << NR];
-  if (sorted)
-    dd_exp_ranges<T, NR>(z, ez, D);
-  else
-    dd_exp_all<T, NR>(z, ez, D);
+  dd_exp_ranges<T, NR>(z, ez, w - 1, D);
   T out[NR];
 #pragma unroll
   for (int i = 0; i < NR; ++i) {

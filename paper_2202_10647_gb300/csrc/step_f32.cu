@@ -909,7 +909,7 @@ __device__ __forceinline__ bool record_cell(const BatchArgs& a, const StagedF32&
   return finish_cell<F32Form, W>(J, a.pol, tab, c, Ec, lo, hi, v, true, change);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     ion_stiff_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ StagedF32 tabs[kMaxJobs];
   // narrow records at [0, nn), wide ones at [cap - nw, cap); thread t < nn_up
@@ -973,33 +973,35 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // FP64-coefficient pass over the queued cells, one cell per thread.
 // ---------------------------------------------------------------------------
+// WM bounds the window width w = hi - lo + 1 (the planes past w are zero).
 // Returns, with ION_CONSERVATION_CHECK, |sum_r v'_r - sum_r v_r| of the
 // window as stored (the inputs summed in FP64 exactly enough: w <= 6 floats).
-template <int W>
+template <int WM>
 __device__ __forceinline__ float fb_cell(const JobIO& J, const Policy& pol,
                                          const StagedF32& tab, int c, int lo, int hi) {
   float* __restrict__ N = static_cast<float*>(J.N);
   const FieldF32 f = field_f32(static_cast<const float*>(J.E)[c]);
-  double v[W], lam[W];
+  const int w = hi - lo + 1;
+  double v[WM], lam[WM];
 #pragma unroll
-  for (int r = 0; r < W; ++r) {
-    v[r] = (double)N[(int64_t)(lo + r) * J.ld + c];
-    lam[r] = (r < W - 1 && !pol.zero_dt) ? (double)rate_dt_f32(tab, lo + r, f) : 0.0;
+  for (int r = 0; r < WM; ++r) {
+    v[r] = r < w ? (double)N[(int64_t)(lo + r) * J.ld + c] : 0.0;
+    lam[r] = (r < w - 1 && !pol.zero_dt) ? (double)rate_dt_f32(tab, lo + r, f) : 0.0;
   }
   double s0 = 0.0;
 #pragma unroll
-  for (int r = 0; r < W; ++r) s0 += v[r];
-  const double dne = dd_update<double, W>(v, lam, W);
-  float vf[W];
+  for (int r = 0; r < WM; ++r) s0 += v[r];
+  const double dne = dd_update<double, WM>(v, lam, w);
+  float vf[WM];
   double s1 = 0.0;
 #pragma unroll
-  for (int r = 0; r < W; ++r) {
+  for (int r = 0; r < WM; ++r) {
     vf[r] = __double2float_rn(v[r]);
-    N[(int64_t)(lo + r) * J.ld + c] = vf[r];
+    if (r < w) N[(int64_t)(lo + r) * J.ld + c] = vf[r];
     s1 += (double)vf[r];
   }
   int nlo = lo, nhi = hi;
-  window_after_step<float, W>(J, pol, vf, W, nlo, nhi);
+  window_after_step<float, WM>(J, pol, vf, w, nlo, nhi);
   const float* G = static_cast<const float*>(J.n_gas);
   const float d = __double2float_rn(dne);
   static_cast<float*>(J.dne)[c] = G ? d * G[c] : d;
@@ -1008,39 +1010,45 @@ __device__ __forceinline__ float fb_cell(const JobIO& J, const Policy& pol,
   return (float)fabs(s1 - s0);
 }
 
+// The queue is dealt out a warp at a time across the blocks (warp k of the
+// grid takes entries 32k..32k+31, and warp k sits in block k mod grid), so
+// that a short queue spreads over as many SMs as it has warps: the FP64 pipe
+// is the bound here, and each SM has its own.  Each warp runs the
+// instantiation of its widest window, so its lanes do not diverge by width.
 __global__ void __launch_bounds__(128) ion_fb_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ StagedF32 tabs[kMaxJobs];
   const unsigned n = *((volatile unsigned*)&a.ws.hdr[kHdrFallback]);
-  if (blockIdx.x * blockDim.x >= n) return;  // no queued cell for this block
+  const unsigned warps = gridDim.x * (blockDim.x / 32u);
+  const unsigned wid = (threadIdx.x / 32u) * gridDim.x + blockIdx.x;  // warp of the grid
+  const unsigned lane = threadIdx.x & 31u;
+  if (blockIdx.x * 32u >= n) return;  // no queued cell for this block
   for (int j = 0; j < a.njobs; ++j) stage_f32(a.job[j].tab, a.pol.log2dt, &tabs[j]);
   __syncthreads();
   uint32_t cmax = 0;  // largest |change of sum_k N_k| (bits), ION_CONSERVATION_CHECK
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += gridDim.x * blockDim.x) {
-    const int c = (int)a.ws.queue[i];
-    const int jid = a.ws.queue_job[i];
-    const JobIO& J = a.job[jid];
-    const StagedF32& tab = tabs[jid];
-    const int lo = J.lo[c], hi = J.hi[c];
+  for (unsigned base = wid * 32u; base < n; base += warps * 32u) {  // warp-uniform
+    const unsigned i = base + lane;
+    int c = 0, jid = 0, lo = 0, hi = -1;
+    if (i < n) {
+      c = (int)a.ws.queue[i];
+      jid = a.ws.queue_job[i];
+      lo = a.job[jid].lo[c];
+      hi = a.job[jid].hi[c];
+    }
+    const int Wm = __reduce_max_sync(kFull, hi - lo + 1);
     float d = 0.0f;
-    switch (hi - lo + 1) {
-      case 2:
+    if (hi >= lo) {
+      const JobIO& J = a.job[jid];
+      const StagedF32& tab = tabs[jid];
+      if (Wm <= 2)
         d = fb_cell<2>(J, a.pol, tab, c, lo, hi);
-        break;
-      case 3:
+      else if (Wm == 3)
         d = fb_cell<3>(J, a.pol, tab, c, lo, hi);
-        break;
-      case 4:
+      else if (Wm == 4)
         d = fb_cell<4>(J, a.pol, tab, c, lo, hi);
-        break;
-      case 5:
+      else if (Wm == 5)
         d = fb_cell<5>(J, a.pol, tab, c, lo, hi);
-        break;
-      case 6:
+      else
         d = fb_cell<6>(J, a.pol, tab, c, lo, hi);
-        break;
-      default:
-        break;
     }
     cmax = max(cmax, abs_bits(d));
   }

@@ -575,17 +575,13 @@ def test_cold_cells_fp64():
     assert np.array_equal(out["lo"], ref["lo"]) and np.array_equal(out["hi"], ref["hi"])
 
 
-def degenerate_cells(sd, n_per=24, seed=3):
-    """Stiff cells (some W dt > 1) whose windows hold a nearly equal pair of
-    rates: at every crossing W_i(E) = W_j(E) with W dt > 1 (found by
-    bisection on the oracle's Eq. 1), fields E (1 + d) for relative offsets d
-    that put the pair's gap |W_i - W_j| / max from 0 to a few 1e-3, in
-    windows of 3 to 6 states that contain both states.  Returns E, N, lo,
-    hi and the oracle's smallest pair gap and largest W dt per cell."""
+def crossings(sd, dt=0.05):
+    """Every field E with W_i(E) = W_j(E) dt > 1 for states i < j <= i + 4
+    (bisection on the oracle's Eq. 1): (i, j, E)."""
     osp = oracle_species(sd)
     Z = sd.Z
     grid = np.exp(np.linspace(math.log(20), math.log(2e5), 20000))
-    Wg = oracle.rates(osp, grid, 0, Z) * 0.05
+    Wg = oracle.rates(osp, grid, 0, Z) * dt
     cross = []
     for i in range(Z):
         for j in range(i + 1, min(Z, i + 5)):
@@ -602,6 +598,19 @@ def degenerate_cells(sd, n_per=24, seed=3):
                     else:
                         b = c
                 cross.append((i, j, a))
+    return cross
+
+
+def degenerate_cells(sd, n_per=24, seed=3):
+    """Stiff cells (some W dt > 1) whose windows hold a nearly equal pair of
+    rates: at every crossing W_i(E) = W_j(E) with W dt > 1 (found by
+    bisection on the oracle's Eq. 1), fields E (1 + d) for relative offsets d
+    that put the pair's gap |W_i - W_j| / max from 0 to a few 1e-3, in
+    windows of 3 to 6 states that contain both states.  Returns E, N, lo,
+    hi and the oracle's smallest pair gap and largest W dt per cell."""
+    osp = oracle_species(sd)
+    Z = sd.Z
+    cross = crossings(sd)
     E, lo, hi = [], [], []
     rel = [0.0, 1e-6, 1e-5, 3e-5, 1e-4, 2e-4, 5e-4, 1e-3, 3e-3, -1e-5, -1e-4, -5e-4]
     for q, (i, j, e0) in enumerate(cross):
@@ -663,3 +672,67 @@ def test_near_degenerate_pairs_take_fp64_coefficients(name):
           f"({sure} with an oracle gap below 5e-4); max |N - oracle| "
           f"{err_fb:.2e} with them, {float(err_nofb[sel].max()):.2e} on the same "
           f"near-degenerate cells without (ION_NO_FP64_FALLBACK)")
+
+
+def end_gap_ratio(lam):
+    """Largest spread / |z_i - z_j| over the contiguous ranges [j, i] of the
+    nodes z = -lam whose spread is at least 1 (1 when the rates fall or rise
+    along the window)."""
+    z = -np.asarray(lam, dtype=np.float64)
+    worst = 1.0
+    for j in range(len(z)):
+        for i in range(j + 2, len(z)):
+            s = z[j:i + 1].max() - z[j:i + 1].min()
+            if s >= 1.0:
+                worst = max(worst, s / max(abs(z[i] - z[j]), 1e-300))
+    return worst
+
+
+@pytest.mark.parametrize("name", ["N", "Ar-like", "Kr-like"])
+def test_close_ends_far_inner_node(name):
+    """Windows whose rates do not fall or rise monotonically and where a
+    range's end rates are close while an inner rate lies far off (near a
+    crossing W_i = W_j, j >= i + 2, with a state between them): the
+    end-removal recurrence of the divided differences would cancel there,
+    so those ranges are evaluated on their sorted nodes.  Relative gaps of
+    2e-3 to 0.1 keep the pair outside the FP64-coefficient criterion.  FP32
+    (with and without the FP64 queue), the FP64-coefficient pass for every
+    stiff cell, and the FP64 form all match the oracle."""
+    sd = {"N": W.nitrogen(), "Ar-like": W.argon_like(), "Kr-like": W.krypton_like()}[name]
+    osp = oracle_species(sd)
+    Z = sd.Z
+    E, lo, hi = [], [], []
+    rel = [2e-3, -2e-3, 5e-3, -5e-3, 1e-2, -1e-2, 3e-2, -3e-2, 0.1, -0.1]
+    for q, (i, j, e0) in enumerate(crossings(sd)):
+        if j < i + 2:
+            continue
+        for r in rel:
+            for w in range(j - i + 2, 7):
+                a = max(0, min(i - (q + w) % 2, Z + 1 - w))
+                if not (a <= i and j <= a + w - 2):
+                    a = max(0, min(i, Z + 1 - w))
+                if a + w - 1 > Z or j > a + w - 2:
+                    continue
+                E.append(float(np.float32(e0 * (1 + r))))
+                lo.append(a)
+                hi.append(a + w - 1)
+    n = len(E)
+    assert n > 0
+    ld = (n + 3) // 4 * 4
+    lo_t = torch.tensor(lo, dtype=torch.uint8)
+    hi_t = torch.tensor(hi, dtype=torch.uint8)
+    N = W.populations(7, lo_t, hi_t.long() - lo_t.long(), Z, ld)
+    Et = torch.tensor(E, dtype=torch.float32)
+    Wc = oracle.rates(osp, Et.double().numpy(), 0, Z) * 0.05
+    ratio = np.array([end_gap_ratio(Wc[lo[c]:hi[c], c]) for c in range(n)])
+    lmax = np.array([Wc[lo[c]:hi[c], c].max() for c in range(n)])
+    far = int(((ratio > 16) & (lmax > 1.01)).sum())
+    assert far >= 10, far
+    for flags in (ionize.ION_F32, ionize.ION_F32 | ionize.ION_NO_FP64_FALLBACK,
+                  ionize.ION_F32 | ionize.ION_FORCE_FP64_COEF, ionize.ION_F64_PLAIN):
+        out, ref = run_both(sd, Et, N, lo_t, hi_t, flags=flags)
+        check(out, ref, lo_t, hi_t, flags)
+        assert out["counters"][1] == 0
+        err = np.abs(out["N"][:, :n] - ref["N"]).max(axis=0)
+        print(f"{name} flags {flags:#x}: {n} cells, {far} stiff with an end-gap ratio "
+              f"above 16 (largest {ratio.max():.3g}); max |N - oracle| {err.max():.2e}")
