@@ -51,6 +51,7 @@ def parse():
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_nitrogen_3d.txt")
+ISSUE_FILE = os.path.join(ROOT, "profiles", "issue_batched_mixed.txt")
 KERNEL_SOURCES = ["paper_2202_10647_gb300/csrc/step_f32.cu",
                   "paper_2202_10647_gb300/csrc/ion_device.cuh",
                   "paper_2202_10647_gb300/csrc/ion_cell.cuh",
@@ -67,21 +68,56 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes of one full-size step from the committed ncu summary, or
-    None when the summary was taken on other kernel sources."""
-    if not os.path.exists(TRAFFIC_FILE):
+def _recorded(path):
+    """key: value lines of a committed ncu record, or None when the record
+    was taken on other kernel sources."""
+    if not os.path.exists(path):
         return None
     kv = {}
-    with open(TRAFFIC_FILE) as f:
+    with open(path) as f:
         for line in f:
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
     if kv.get("sources_sha256") != kernel_sources_hash():
         return None
+    return kv
+
+
+def batched_issue_roofline(ms, sm_mhz, num_sms):
+    """Issue roofline of the batched step: the warp instructions of one step
+    (committed ncu record) against 4 warp instructions per SM cycle at the
+    SM clock sampled during the run, and each kernel's share."""
+    kv = _recorded(ISSUE_FILE)
+    if kv is None or not sm_mhz:
+        return None
     try:
-        return int(kv["dram_bytes_per_step"])
+        inst = float(kv["warp_inst_per_step"])
+        per = {k: (float(kv[f"{k}_warp_inst"]), float(kv[f"{k}_us"]))
+               for k in ("stream", "stiff", "fb")}
+        scale = float(kv["scale"])
+    except (KeyError, ValueError):
+        return None
+    peak = num_sms * 4 * sm_mhz * 1e6  # warp instructions per second
+    achieved = inst / (ms * 1e-3)
+    kernels = {}
+    for k, (ki, kus) in per.items():
+        # in the capture: the kernel's own issue rate against the ceiling
+        kernels[f"ion_{k}_kernel"] = {
+            "warp_inst_per_step": ki * scale,
+            "issue_frac_in_capture": ki / (kus * 1e-6) / peak if kus > 0 else None}
+    return {"bound": "issue", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "G warp instructions/s", "frac": achieved / peak,
+            "warp_inst_per_step": inst, "kernels": kernels,
+            "record": os.path.relpath(ISSUE_FILE, ROOT)}
+
+
+def recorded_traffic():
+    """DRAM bytes of one full-size step from the committed ncu summary, or
+    None when the summary was taken on other kernel sources."""
+    kv = _recorded(TRAFFIC_FILE)
+    try:
+        return None if kv is None else int(kv["dram_bytes_per_step"])
     except (KeyError, ValueError):
         return None
 
@@ -771,6 +807,10 @@ def main():
     if rank != 0:
         return
     clocks = clk.summary()
+    if batched is not None:
+        batched["roofline"] = batched_issue_roofline(
+            batched["ms_per_step"], clocks.get("sm_mhz") or clocks.get("sm_max_mhz"),
+            torch.cuda.get_device_properties(dev).multi_processor_count)
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

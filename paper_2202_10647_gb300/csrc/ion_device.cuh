@@ -331,7 +331,7 @@ struct DDParams<float> {
   static constexpr float prop_max = 1.0f;  // Taylor propagation up to max W dt
   static constexpr int PMAX = 16;      // terms needed at 2 * prop_max
   static constexpr bool kUniform = true;  // every Taylor term up to RMAX
-  static constexpr float end_ratio = 8.0f;  // dd_exp_ranges' recurrence bound
+  static constexpr float end_ratio = 4.0f;  // dd_exp_ranges' recurrence bound
   __device__ static __forceinline__ int terms(float x, int rmax) {
     int R = 0;
 #pragma unroll
@@ -350,7 +350,7 @@ struct DDParams<double> {
   static constexpr double prop_max = 0.5;
   static constexpr int PMAX = 18;
   static constexpr bool kUniform = false;  // terms(s) of them
-  static constexpr double end_ratio = 8.0;
+  static constexpr double end_ratio = 4.0;
   __device__ static __forceinline__ int terms(double x, int rmax) {
     int R = 0;
 #pragma unroll
@@ -414,10 +414,15 @@ __device__ __noinline__ T dd_set(T z0, T z1, T z2, T z3, T z4, T e0, T e1, T e2,
 // them instead of the 2^NR - NR - 1 subsets of a recurrence that removes the
 // smallest and the largest node).  When the range's ends are its extremes
 // (rates falling or rising along the window) that is the same recurrence.
-// Otherwise the two terms can cancel: their relative difference is about
-// |z_i - z_j| / spread, so a live range (i < nlive; nodes past nlive are not
-// read by dd_update) whose spread exceeds END_RATIO |z_i - z_j| is evaluated
-// on its own nodes sorted (dd_set).
+// Otherwise the two terms can cancel.  Each term is about (len-1) D[j..i]
+// when the nodes lie within a few units and about (2 max z - z_i - z_j)
+// D[j..i] for a wide range, and their difference is |z_i - z_j| D[j..i]; the
+// ratio, the factor by which the subtraction magnifies the terms' rounding,
+// stays below 2 END_RATIO (as with sorted nodes, whose end gap is the
+// spread) while |z_i - z_j| >= TAU and the spread is at most
+// END_RATIO |z_i - z_j|.  A live range (i < nlive; nodes past nlive are not
+// read by dd_update) outside those bounds is evaluated on its own nodes
+// sorted (dd_set).
 template <typename T, int NR>
 __device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR], int nlive,
                                               T (&D)[1 << NR]) {
@@ -459,7 +464,8 @@ __device__ __forceinline__ void dd_exp_ranges(const T (&z)[NR], const T (&ez)[NR
       T d;
       if (s < P::tau) {
         d = ez[j] * C[j][i];
-      } else if (len > 2 && i < nlive && s > P::end_ratio * fabs(dz)) {
+      } else if (len > 2 && i < nlive &&
+                 (fabs(dz) < P::tau || s > P::end_ratio * fabs(dz))) {
         // the range's own nodes, padded with z = 0 (the largest a node can be)
         d = dd_set<T>(z[j], z[j + 1], z[j + 2 < NR ? j + 2 : j],
                       len > 3 ? z[j + 3 < NR ? j + 3 : j] : T(0),
