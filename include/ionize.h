@@ -42,7 +42,7 @@ extern "C" {
 #define ION_OK 0
 #define ION_EINVAL (-1)   /* bad argument (null, range, alignment, size)     */
 #define ION_ECUDA (-2)    /* a CUDA call or kernel launch failed              */
-#define ION_ENOMEM (-3)   /* allocation failed (species creation only)        */
+#define ION_ENOMEM (-3)   /* allocation failed (creation and validation calls) */
 #define ION_ETIMEOUT (-4) /* a bounded device-side wait gave up               */
 
 /* ---- flags of ion_step --------------------------------------------------- */
@@ -371,6 +371,44 @@ ION_API int ion_mlp_adam(float* P, const float* grad, float* m, float* v, int64_
 ION_API int ion_mlp_forward(const float* P, int K, const float* x, int64_t B, int flags,
                             float* y, void* stream);
 
+/* ---- rate surrogate: training data ---------------------------------------
+ * The arithmetic that turns fields and rates into the network's inputs and
+ * targets (the paper has no counterpart; the targets are Eq. 1 itself). */
+
+/* ion_log2_rates -- the training targets: max(log2 W_k(|E_c|), floor) with
+ * W_k of Eq. 1 in 1/fs, evaluated in FP64 in its log2 form (the exponent
+ * a_k - b_k log2|E| - C_k/|E| itself, no exp2/log2 round trip); floor where
+ * W_k is 0 (|E| below 1e-6 GV/m, or past the exponent cutoff of Eq. 1).
+ *   E     device float [ncells] fields in GV/m (sign ignored).
+ *   out   device double, out[c*ldo + (k - k_lo)] for k_lo <= k < k_hi
+ *         (cell-major: one row of rates per sample), ldo >= k_hi - k_lo.
+ * 0 <= k_lo < k_hi <= Z; 0 <= ncells < 2^31; the species' device is
+ * current.  Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_log2_rates(const ion_species* sp, const float* E, int64_t ncells, int k_lo,
+                           int k_hi, double floor, double* out, int64_t ldo, void* stream);
+
+/* ion_mlp_inputs -- the network's input x_c = clamp(2 (log2|E_c| - l2lo) /
+ * (l2hi - l2lo) - 1, -1, 1), computed in FP64 and rounded to float, as the
+ * inference kernels map |E| (log2 of 0 is -infinity, so x = -1).
+ *   E, x  device float [n], 0 <= n < 2^40; finite l2lo < l2hi.
+ * Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_mlp_inputs(const float* E, int64_t n, double l2lo, double l2hi, float* x,
+                           void* stream);
+
+/* ion_mlp_standardize -- per-column standardization of the targets:
+ *   mean_k = (1/n) sum_c Y[c*K + k],
+ *   scale_k = max(sqrt(sum_c (Y[c*K + k] - mean_k)^2 / (n - 1)), min_scale),
+ *   T[c*K + k] = (float)((Y[c*K + k] - mean_k) / scale_k).
+ *   Y          device double [n*K] (cell-major, as ion_log2_rates writes).
+ *   mean_out,
+ *   scale_out  device double [K].
+ *   T          device float [n*K].
+ * 2 <= n < 2^32, 1 <= K <= ION_MAX_Z, min_scale > 0.  The sums run in
+ * FP64 in a fixed order, one block of threads per column (equal inputs give
+ * equal bits).  Allocates nothing.  Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_mlp_standardize(const double* Y, int64_t n, int K, double min_scale,
+                                double* mean_out, double* scale_out, float* T, void* stream);
+
 /* ---- rate surrogate: inference -------------------------------------------
  * A trained network (parameters as above, K = Z outputs) becomes an
  * ion_surrogate: W2 and W3 in bf16 laid out for the tensor cores, the other
@@ -455,6 +493,25 @@ ION_API int ion_step_surrogate(const ion_surrogate* s, const float* E, float* N,
  * memory.  on = 0 restores the normal waits.  Synchronous (one 4-byte copy
  * to the device).  Errors: ION_EINVAL, ION_ECUDA. */
 ION_API int ion_surrogate_test_timeout(ion_surrogate* s, int on);
+
+/* ion_surrogate_validate -- the validation error bound, computed on the GPU
+ * and installed in the surrogate (replacing any bound it had): the trained
+ * range [log2E_min, log2E_max] is split into nbins equal bins; bin b is
+ * sampled at per_bin points l2 = log2E_min + (log2E_max - log2E_min)
+ * (b + i/(per_bin - 1))/nbins, i = 0..per_bin-1 (both edges included), at
+ * E = (float)2^l2.  There the network's rates (as ion_surrogate_rates gives
+ * them) and Eq. 1's in FP64 are compared in log2, both clamped below at
+ * y_floor:
+ *   bound[b*Z + k] = margin * max_i |log2 W_k(net) - log2 W_k| + floor_add.
+ *   bound_out  host float [nbins*Z] or NULL: a copy of the bound.
+ * 1 <= nbins <= 65536, 2 <= per_bin <= 4096, nbins * per_bin <= 2^24,
+ * finite margin >= 1 and floor_add >= 0.  Allocates and frees device
+ * scratch (about 4 (Z + 1) nbins per_bin bytes) and synchronizes the
+ * stream; not to be called while another call uses the surrogate.  A bounded tensor-core wait that gives up makes
+ * the call fail (ION_ETIMEOUT) and leaves the old bound.
+ * Errors: ION_EINVAL, ION_ENOMEM, ION_ECUDA, ION_ETIMEOUT. */
+ION_API int ion_surrogate_validate(ion_surrogate* s, int nbins, int per_bin, double margin,
+                                   double floor_add, float* bound_out, void* stream);
 
 /* ion_measure_peaks -- throughput of the current device for the arithmetic
  * the step's forms are bound by, from loops of independent dependency chains

@@ -110,6 +110,17 @@ __global__ void rates_f64_kernel(const ion::SpeciesTable* t, const double* E,
     W[(int64_t)(k - k_lo) * ldw + c] = ion::rate_dt_f64(tab, k, f);
 }
 
+__global__ void log2_rates_kernel(const ion::SpeciesTable* t, const float* E, int64_t ncells,
+                                  int k_lo, int k_hi, double floor, double* out, int64_t ldo) {
+  __shared__ ion::StagedF64 tab;
+  ion::stage_f64(t, 0.0, &tab);
+  __syncthreads();
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const ion::FieldF64 f = ion::field_f64((double)E[c]);
+  for (int k = k_lo; k < k_hi; ++k) out[c * ldo + (k - k_lo)] = ion::log2_rate_f64(tab, k, f, floor);
+}
+
 int check_species(const ion_species* sp) {
   if (!sp || !sp->dev) return fail(ION_EINVAL, "species is NULL or destroyed");
   return ION_OK;
@@ -219,6 +230,32 @@ int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int k_lo,
                                                 static_cast<double*>(W_out), ldw);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ok() : cuda_fail(e, "ion_rates launch");
+}
+
+int ion_log2_rates(const ion_species* sp, const float* E, int64_t ncells, int k_lo, int k_hi,
+                   double floor, double* out, int64_t ldo, void* stream) {
+  int rc = check_species(sp);
+  if (rc) return rc;
+  if (ncells < 0 || ncells >= (int64_t(1) << 31))
+    return fail(ION_EINVAL, "ncells=%lld outside [0, 2^31)", (long long)ncells);
+  if (k_lo < 0 || k_hi > sp->Z || k_lo >= k_hi)
+    return fail(ION_EINVAL, "need 0 <= k_lo < k_hi <= Z (k_lo=%d, k_hi=%d, Z=%d)", k_lo, k_hi,
+                sp->Z);
+  if (!std::isfinite(floor)) return fail(ION_EINVAL, "floor must be finite");
+  if (ncells == 0) return ok();
+  if (!E || !out) return fail(ION_EINVAL, "E and out must be non-NULL");
+  if ((reinterpret_cast<uintptr_t>(E) & 3u) || (reinterpret_cast<uintptr_t>(out) & 7u))
+    return fail(ION_EINVAL, "E must be 4-byte and out 8-byte aligned");
+  if (ldo < k_hi - k_lo) return fail(ION_EINVAL, "ldo=%lld < k_hi - k_lo", (long long)ldo);
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != sp->device)
+    return fail(ION_EINVAL, "the species lives on device %d; make it current", sp->device);
+  const int threads = 256;
+  const int64_t blocks = (ncells + threads - 1) / threads;
+  log2_rates_kernel<<<(unsigned)blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+      sp->dev, E, ncells, k_lo, k_hi, floor, out, ldo);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ok() : cuda_fail(e, "ion_log2_rates launch");
 }
 
 size_t ion_step_workspace_bytes(int64_t ncells, int flags) {

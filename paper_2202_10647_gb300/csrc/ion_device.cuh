@@ -268,6 +268,16 @@ __device__ __forceinline__ double rate_dt_f64(const StagedF64& t, int k, double 
   return rate_dt_f64(t, k, field_f64(E_in));
 }
 
+// log2(W_k dt) in FP64 straight from the exponent of rate_dt_f64 (no exp2 /
+// log2 round trip), clamped below at `floor`, which also stands for W = 0.
+__device__ __forceinline__ double log2_rate_f64(const StagedF64& t, int k, const FieldF64& f,
+                                                double floor) {
+  if (f.zero) return floor;
+  const double q = t.C[k] * f.rE;
+  if (q > kCutoffLog2) return floor;
+  return fmax(fmin(t.a[k] - t.b[k] * f.lg - q, 1000.0), floor);
+}
+
 // ---------------------------------------------------------------------------
 // Divided differences of exp.
 //

@@ -348,6 +348,52 @@ int check_common(const char* who, const float* P, int K, const float* x, int64_t
   return ION_OK;
 }
 
+// ---- training data ---------------------------------------------------------
+// x = clamp(2 (log2|E| - l2lo) / (l2hi - l2lo) - 1, -1, 1) in FP64.
+__global__ void mlp_inputs_kernel(const float* E, int64_t n, double l2lo, double l2hi,
+                                  float* x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l2 = log2(fabs((double)E[i]));
+  const double v = 2.0 * (l2 - l2lo) / (l2hi - l2lo) - 1.0;
+  x[i] = (float)fmin(fmax(v, -1.0), 1.0);  // fmax of NaN and -1 is -1
+}
+
+constexpr int kColThreads = 1024;
+
+// One block per column k of Y (n rows of K): the sum over the rows in a
+// fixed order (thread t takes rows t, t + 1024, ...; then a tree over the
+// threads).  Without `mean`: out[k] = sum / n.  With it: out[k] =
+// max(sqrt(sum (Y - mean_k)^2 / (n - 1)), min_scale).
+__global__ void __launch_bounds__(kColThreads)
+    mlp_column_kernel(const double* Y, int64_t n, int K, const double* mean, double min_scale,
+                      double* out) {
+  __shared__ double part[kColThreads];
+  const int k = blockIdx.x;
+  const double m = mean ? mean[k] : 0.0;
+  double acc = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += kColThreads) {
+    const double d = Y[r * K + k] - m;
+    acc += mean ? d * d : d;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kColThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    out[k] = mean ? fmax(sqrt(part[0] / (double)(n - 1)), min_scale) : part[0] / (double)n;
+}
+
+__global__ void mlp_normalize_kernel(const double* Y, int64_t n, int K, const double* mean,
+                                     const double* scale, float* T) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * K) return;
+  const int k = (int)(i % K);
+  T[i] = (float)((Y[i] - mean[k]) / scale[k]);
+}
+
 }  // namespace
 }  // namespace mlp
 }  // namespace ion
@@ -454,6 +500,52 @@ int ion_mlp_forward(const float* P, int K, const float* x, int64_t B, int flags,
   }
   if (e != cudaSuccess)
     return ion::set_error(ION_ECUDA, "ion_mlp_forward launch: %s", cudaGetErrorString(e));
+  return ion::set_error(ION_OK, "%s", "");
+}
+
+int ion_mlp_inputs(const float* E, int64_t n, double l2lo, double l2hi, float* x,
+                   void* stream) {
+  if (n < 0 || n >= (int64_t(1) << 40))
+    return ion::set_error(ION_EINVAL, "ion_mlp_inputs: n=%lld outside [0, 2^40)",
+                          (long long)n);
+  if (!(l2lo < l2hi) || !std::isfinite(l2lo) || !std::isfinite(l2hi))
+    return ion::set_error(ION_EINVAL, "ion_mlp_inputs: need finite l2lo < l2hi");
+  if (n == 0) return ion::set_error(ION_OK, "%s", "");
+  if (!E || !x || (reinterpret_cast<uintptr_t>(E) & 3u) || (reinterpret_cast<uintptr_t>(x) & 3u))
+    return ion::set_error(ION_EINVAL, "ion_mlp_inputs: E and x must be non-NULL, 4-byte aligned");
+  const int64_t blocks = (n + 255) / 256;
+  mlp_inputs_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      E, n, l2lo, l2hi, x);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return ion::set_error(ION_ECUDA, "ion_mlp_inputs launch: %s", cudaGetErrorString(e));
+  return ion::set_error(ION_OK, "%s", "");
+}
+
+int ion_mlp_standardize(const double* Y, int64_t n, int K, double min_scale, double* mean_out,
+                        double* scale_out, float* T, void* stream) {
+  if (n < 2 || n >= (int64_t(1) << 32))
+    return ion::set_error(ION_EINVAL, "ion_mlp_standardize: n=%lld outside [2, 2^32)",
+                          (long long)n);
+  if (K < 1 || K > ION_MAX_Z)
+    return ion::set_error(ION_EINVAL, "ion_mlp_standardize: K=%d outside [1, %d]", K,
+                          ION_MAX_Z);
+  if (!(min_scale > 0.0) || !std::isfinite(min_scale))
+    return ion::set_error(ION_EINVAL, "ion_mlp_standardize: min_scale must be finite and > 0");
+  auto al = [](const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; };
+  if (!Y || !mean_out || !scale_out || !T || !al(Y, 8) || !al(mean_out, 8) ||
+      !al(scale_out, 8) || !al(T, 4))
+    return ion::set_error(ION_EINVAL,
+                          "ion_mlp_standardize: Y, mean_out, scale_out (8-byte aligned) and T "
+                          "(4-byte aligned) must be non-NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mlp_column_kernel<<<K, kColThreads, 0, s>>>(Y, n, K, nullptr, min_scale, mean_out);
+  mlp_column_kernel<<<K, kColThreads, 0, s>>>(Y, n, K, mean_out, min_scale, scale_out);
+  const int64_t blocks = (n * K + 255) / 256;
+  mlp_normalize_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, n, K, mean_out, scale_out, T);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return ion::set_error(ION_ECUDA, "ion_mlp_standardize launch: %s", cudaGetErrorString(e));
   return ion::set_error(ION_OK, "%s", "");
 }
 

@@ -489,6 +489,46 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
                  : "memory");
 }
 
+// ---- validation error bound (ion_surrogate_validate) ----------------------
+// Sample points: bin b, point i at log2|E| = l2lo + (l2hi - l2lo)
+// (b + i/(per_bin - 1))/nbins, rounded to float.
+__global__ void bound_points_kernel(int nbins, int per_bin, double l2lo, double l2hi, float* E) {
+  const int64_t n = (int64_t)nbins * per_bin;
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t b = j / per_bin;
+  const int i = (int)(j - b * per_bin);
+  const double l2 = l2lo + (l2hi - l2lo) * ((double)b + (double)i / (per_bin - 1)) / nbins;
+  E[j] = (float)exp2(l2);
+}
+
+// One thread per (bin, state): margin * max over the bin's points of
+// |max(log2 W_net, floor) - max(log2 W, floor)| + floor_add, W from Eq. 1 in
+// FP64.  A NaN network rate (a tensor-core wait that gave up) sets *bad.
+__global__ void bound_kernel(const SpeciesTable* t, const float* E, const float* Wn, int64_t ld,
+                             int nbins, int per_bin, int Z, double floor, double margin,
+                             double floor_add, float* bound, unsigned* bad) {
+  __shared__ StagedF64 tab;
+  stage_f64(t, 0.0, &tab);
+  __syncthreads();
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= (int64_t)nbins * Z) return;
+  const int64_t b = q / Z;
+  const int k = (int)(q - b * Z);
+  double d = 0.0;
+  bool nan = false;
+  for (int i = 0; i < per_bin; ++i) {
+    const int64_t j = b * per_bin + i;
+    const double yt = log2_rate_f64(tab, k, field_f64((double)E[j]), floor);
+    const float w = Wn[(int64_t)k * ld + j];
+    nan = nan || isnan(w);
+    const double yn = w > 0.0f ? fmax(log2((double)w), floor) : floor;
+    d = fmax(d, fabs(yn - yt));
+  }
+  if (nan) atomicOr(bad, 1u);
+  bound[q] = (float)(d * margin + floor_add);
+}
+
 }  // namespace sg
 }  // namespace ion
 
@@ -500,6 +540,7 @@ struct ion_surrogate {
   int fit_rates, fit_step;  // resident CTAs per SM of the two kernels
   ion::sg::Dev* dev;
   float* bound;  // device [nbins][Z] of 2^bound - 1, or nullptr
+  ion_surrogate_norm norm;
 };
 
 namespace {
@@ -593,6 +634,44 @@ int check_surrogate(const ion_surrogate* s) {
 
 bool al4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
+// Replaces the surrogate's bound by the host array b [nbins*Z] (log2 units):
+// the device copy holds 2^b - 1, and the bin mapping of the kernels' Consts
+// follows nbins.  Synchronous.
+int install_bound(ion_surrogate* s, const float* b, int nbins) {
+  const size_t m = (size_t)nbins * s->Z;
+  std::vector<float> beta(m);
+  for (size_t i = 0; i < m; ++i) {
+    if (!(b[i] >= 0.0f) || !std::isfinite(b[i]))
+      return ion::set_error(ION_EINVAL, "bound[%zu] must be finite and >= 0", i);
+    beta[i] = (float)(std::exp2((double)b[i]) - 1.0);
+  }
+  float* dst = nullptr;
+  cudaError_t e = cudaMalloc(&dst, sizeof(float) * m);
+  if (e == cudaSuccess) e = cudaMemcpy(dst, beta.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
+  const double span = s->norm.log2E_max - s->norm.log2E_min;
+  const float bin_a = (float)(nbins / span);
+  const float bin_b = (float)(-s->norm.log2E_min * nbins / span);
+  char* k = reinterpret_cast<char*>(s->dev) + offsetof(Dev, k);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(k + offsetof(ion::sg::Consts, bin_a), &bin_a, sizeof bin_a,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(k + offsetof(ion::sg::Consts, bin_b), &bin_b, sizeof bin_b,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(k + offsetof(ion::sg::Consts, nbins), &nbins, sizeof nbins,
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (dst) cudaFree(dst);
+    return ion::set_error(e == cudaErrorMemoryAllocation ? ION_ENOMEM : ION_ECUDA,
+                          "installing the bound: %s", cudaGetErrorString(e));
+  }
+  if (s->bound) cudaFree(s->bound);
+  s->bound = dst;
+  s->nbins = nbins;
+  return ION_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -680,6 +759,7 @@ int ion_surrogate_create(const ion_species* sp, const float* P, const ion_surrog
   s->nbins = nbins;
   s->dev = nullptr;
   s->bound = nullptr;
+  s->norm = *norm;
   e = cudaMalloc(&s->dev, sizeof(Dev));
   if (e == cudaSuccess) e = cudaMemcpy(s->dev, img, sizeof(Dev), cudaMemcpyHostToDevice);
   delete img;
@@ -711,6 +791,71 @@ int ion_surrogate_test_timeout(ion_surrogate* s, int on) {
   if (e != cudaSuccess)
     return ion::set_error(ION_ECUDA, "ion_surrogate_test_timeout: %s", cudaGetErrorString(e));
   return ion::set_error(ION_OK, "%s", "");
+}
+
+int ion_surrogate_validate(ion_surrogate* s, int nbins, int per_bin, double margin,
+                           double floor_add, float* bound_out, void* stream) {
+  using namespace ion;
+  int rc = check_surrogate(s);
+  if (rc) return rc;
+  if (nbins < 1 || nbins > 65536 || per_bin < 2 || per_bin > 4096 ||
+      (int64_t)nbins * per_bin > (int64_t(1) << 24))
+    return set_error(ION_EINVAL,
+                     "need 1 <= nbins <= 65536, 2 <= per_bin <= 4096, nbins*per_bin <= 2^24");
+  if (!(margin >= 1.0) || !std::isfinite(margin) || !(floor_add >= 0.0) ||
+      !std::isfinite(floor_add))
+    return set_error(ION_EINVAL, "need finite margin >= 1 and floor_add >= 0");
+  const int Z = s->Z;
+  const int64_t n = (int64_t)nbins * per_bin;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t oE = 0, oW = up(4 * (size_t)n), oB = oW + up(4 * (size_t)n * Z),
+               oF = oB + up(4 * (size_t)nbins * Z), total = oF + 256;
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, total);
+  if (e != cudaSuccess)
+    return set_error(e == cudaErrorMemoryAllocation ? ION_ENOMEM : ION_ECUDA,
+                     "ion_surrogate_validate scratch: %s", cudaGetErrorString(e));
+  float* Eg = reinterpret_cast<float*>(buf + oE);
+  float* Wn = reinterpret_cast<float*>(buf + oW);
+  float* bd = reinterpret_cast<float*>(buf + oB);
+  unsigned* bad = reinterpret_cast<unsigned*>(buf + oF);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<float> hb((size_t)nbins * Z);
+  unsigned hbad = 0;
+  e = cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) {
+    sg::bound_points_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        nbins, per_bin, s->norm.log2E_min, s->norm.log2E_max, Eg);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.W_out = Wn;
+    a.ldw = n;
+    a.ncells = n;
+    a.E = Eg;
+    e = launch(s, false, a, st);
+  }
+  if (e == cudaSuccess) {
+    const int64_t q = (int64_t)nbins * Z;
+    sg::bound_kernel<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(
+        &s->dev->tab, Eg, Wn, n, nbins, per_bin, Z, s->norm.y_floor, margin, floor_add, bd, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hb.data(), bd, sizeof(float) * hb.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess)
+    return set_error(ION_ECUDA, "ion_surrogate_validate: %s", cudaGetErrorString(e));
+  if (hbad)
+    return set_error(ION_ETIMEOUT, "ion_surrogate_validate: a tensor-core wait gave up");
+  if ((rc = install_bound(s, hb.data(), nbins))) return rc;
+  if (bound_out) std::memcpy(bound_out, hb.data(), sizeof(float) * hb.size());
+  return set_error(ION_OK, "%s", "");
 }
 
 int ion_surrogate_destroy(ion_surrogate* s) {

@@ -40,8 +40,10 @@ EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_step_batched_workspace_bytes", "ion_step_batched", "ion_autotune",
            "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
            "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
+           "ion_log2_rates", "ion_mlp_inputs", "ion_mlp_standardize",
            "ion_surrogate_create", "ion_surrogate_destroy", "ion_surrogate_rates",
-           "ion_step_surrogate", "ion_surrogate_test_timeout", "ion_measure_peaks",
+           "ion_step_surrogate", "ion_surrogate_test_timeout", "ion_surrogate_validate",
+           "ion_measure_peaks",
            "ion_binary_version",
            "ion_last_error")
 
@@ -173,6 +175,14 @@ def _declare(lib):
                                  ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp]
     lib.ion_mlp_forward.restype = ctypes.c_int
     lib.ion_mlp_forward.argtypes = [_vp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]
+    lib.ion_log2_rates.restype = ctypes.c_int
+    lib.ion_log2_rates.argtypes = [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   _vp, _i64, _vp]
+    lib.ion_mlp_inputs.restype = ctypes.c_int
+    lib.ion_mlp_inputs.argtypes = [_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp]
+    lib.ion_mlp_standardize.restype = ctypes.c_int
+    lib.ion_mlp_standardize.argtypes = [_vp, _i64, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp,
+                                        _vp]
     lib.ion_surrogate_create.restype = ctypes.c_int
     lib.ion_surrogate_create.argtypes = [_vp, _vp, ctypes.POINTER(_SurrogateNorm),
                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int,
@@ -187,6 +197,9 @@ def _declare(lib):
                                        _vp, ctypes.c_size_t, _vp]
     lib.ion_surrogate_test_timeout.restype = ctypes.c_int
     lib.ion_surrogate_test_timeout.argtypes = [_vp, ctypes.c_int]
+    lib.ion_surrogate_validate.restype = ctypes.c_int
+    lib.ion_surrogate_validate.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, _vp, _vp]
     lib.ion_measure_peaks.restype = ctypes.c_int
     lib.ion_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.ion_binary_version.restype = ctypes.c_int
@@ -222,6 +235,10 @@ def _check(rc: int):
 
 def _stream(t: torch.Tensor):
     return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _stream_of(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
 def _ptr(t, offset: int = 0):
@@ -554,6 +571,48 @@ def mlp_forward(P: torch.Tensor, K: int, x: torch.Tensor, flags: int = 0,
     return out
 
 
+def log2_rates(sp: Species, E: torch.Tensor, k_lo: int, k_hi: int, floor: float,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """ion_log2_rates: max(log2 W_k(|E|), floor) in FP64 for k in [k_lo, k_hi),
+    tensor (ncells, k_hi - k_lo) float64 (one row per cell)."""
+    _need(E, "E", torch.float32)
+    n = E.numel()
+    if out is None:
+        out = torch.empty((n, k_hi - k_lo), dtype=torch.float64, device=E.device)
+    _need(out, "out", torch.float64, E.device)
+    if out.dim() != 2 or out.shape[0] != n or out.stride(1) != 1:
+        raise ValueError("out must be (ncells, k_hi - k_lo) with unit column stride")
+    _check(lib().ion_log2_rates(sp.handle, _ptr(E), n, int(k_lo), int(k_hi), float(floor),
+                                _ptr(out), out.stride(0), _stream(E)))
+    return out
+
+
+def mlp_inputs(E: torch.Tensor, l2lo: float, l2hi: float,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """ion_mlp_inputs: the network input of each field, float32 [n]."""
+    _need(E, "E", torch.float32)
+    out = torch.empty(E.numel(), dtype=torch.float32, device=E.device) if out is None else out
+    _need(out, "out", torch.float32, E.device)
+    _check(lib().ion_mlp_inputs(_ptr(E), E.numel(), float(l2lo), float(l2hi), _ptr(out),
+                                _stream(E)))
+    return out
+
+
+def mlp_standardize(Y: torch.Tensor, min_scale: float):
+    """ion_mlp_standardize of targets Y (n, K) float64: (mean [K], scale [K],
+    T (n, K) float32), all on Y's device."""
+    _need(Y, "Y", torch.float64)
+    if Y.dim() != 2:
+        raise ValueError("Y must be (n, K)")
+    n, K = Y.shape
+    mean = torch.empty(K, dtype=torch.float64, device=Y.device)
+    scale = torch.empty(K, dtype=torch.float64, device=Y.device)
+    T = torch.empty((n, K), dtype=torch.float32, device=Y.device)
+    _check(lib().ion_mlp_standardize(_ptr(Y), n, K, float(min_scale), _ptr(mean), _ptr(scale),
+                                     _ptr(T), _stream(Y)))
+    return mean, scale, T
+
+
 class Surrogate:
     """ion_surrogate_create: a trained network for species `sp`.
 
@@ -601,6 +660,19 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+    def validate(self, nbins: int = 4096, per_bin: int = 64, margin: float = 1.25,
+                 floor_add: float = 2e-3):
+        """ion_surrogate_validate: compute the validation bound on the GPU and
+        install it; returns it as a numpy array (nbins, Z)."""
+        import numpy as _np
+        b = _np.empty((int(nbins), self.Z), dtype=_np.float32)
+        _check(lib().ion_surrogate_validate(self._h, int(nbins), int(per_bin), float(margin),
+                                            float(floor_add),
+                                            b.ctypes.data_as(ctypes.c_void_p),
+                                            _stream_of(self.device)))
+        self._bound = b
+        return b
 
     def test_timeout(self, on: bool = True) -> None:
         """ion_surrogate_test_timeout: make the kernels' first tensor-core

@@ -1,30 +1,27 @@
 """Training and validation of the rate surrogate (the learned alternative to
 evaluating Eq. 1 per state).
 
-Pipeline (every arithmetic step on the GPU runs in the library's kernels;
-torch only holds the tensors, draws the batch order and does the elementwise
-scaling of inputs and targets):
+Pipeline (every arithmetic step runs in the library's kernels; torch holds
+the tensors, draws the batch order and gathers the batches):
 
-  training_set   |E| with log10|E| ~ U[1, 5] (GV/m) from the counter-based
-                 hash, the rates of every state from ion_rates in FP64 (the
-                 plain evaluation of Eq. 1), targets log2 W clamped below at
-                 y_floor.
-  train          Adam on the mean squared error of the standardized targets
+  training_set   |E| with log10|E| ~ U[1, 5] (GV/m) from the seeded input
+                 generator, targets max(log2 W_k, y_floor) for every state
+                 from ion_log2_rates (Eq. 1 in FP64, in its log2 form).
+  train          inputs from ion_mlp_inputs, targets standardized per state
+                 by ion_mlp_standardize; Adam on the mean squared error
                  (ion_mlp_loss_grad, ion_mlp_adam), the last steps in the
                  inference arithmetic (bf16, straight-through).
-  error_bound    the tensor-core network (ion_surrogate_rates) against
-                 ion_rates in FP64 on a dense grid: per input bin and state,
-                 the largest |log2 W_net - log2 W| (both clamped at y_floor),
-                 widened by a safety margin.
-  build          train, bound, and return the ion_surrogate that
-                 ion_step_surrogate uses.
+  build          train, then ion_surrogate_validate: the tensor-core network
+                 against Eq. 1 in FP64 on a dense grid, per input bin and
+                 state the largest |log2 W_net - log2 W| (both clamped at
+                 y_floor), widened by a safety margin, installed as the
+                 bound that ion_step_surrogate trusts the network by.
 """
 from __future__ import annotations
 
 import math
 from dataclasses import dataclass
 
-import numpy as np
 import torch
 
 from . import ionize
@@ -39,24 +36,21 @@ def log2_range(log10E=LOG10E_RANGE):
 
 
 def scaled_input(E: torch.Tensor, l2lo: float, l2hi: float) -> torch.Tensor:
-    """x = 2 (log2|E| - l2lo)/(l2hi - l2lo) - 1, float32."""
-    l2 = torch.log2(E.abs().double())
-    return (2.0 * (l2 - l2lo) / (l2hi - l2lo) - 1.0).to(torch.float32)
+    """x = clamp(2 (log2|E| - l2lo)/(l2hi - l2lo) - 1, -1, 1), float32
+    (ion_mlp_inputs)."""
+    return ionize.mlp_inputs(E.to(torch.float32).contiguous(), l2lo, l2hi)
 
 
 def plain_log2_rates(sp: ionize.Species, E: torch.Tensor, floor: float = Y_FLOOR):
     """max(log2 W_k(|E|), floor) for every state, (n, Z) float64, from
-    ion_rates in FP64."""
-    Wt = ionize.rates(sp, E.double().contiguous(), 0, sp.Z)  # (Z, n)
-    return torch.log2(Wt).clamp(min=floor).T.contiguous()
+    ion_log2_rates (Eq. 1 in FP64)."""
+    return ionize.log2_rates(sp, E.to(torch.float32).contiguous(), 0, sp.Z, floor)
 
 
 def training_set(sp: ionize.Species, n: int = 1 << 20, seed: int = 11,
                  log10E=LOG10E_RANGE, device="cuda"):
     """(E float32 [n], log2 W float64 [n, Z])."""
-    idx = torch.arange(n, device=device, dtype=torch.int64)
-    u = W.uniform(seed, 60, idx)
-    E = torch.pow(10.0, log10E[0] + (log10E[1] - log10E[0]) * u).to(torch.float32)
+    E = W.log_uniform_fields(seed, 60, n, log10E[0], log10E[1], device=device)
     return E, plain_log2_rates(sp, E)
 
 
@@ -94,9 +88,7 @@ def train(sp: ionize.Species, n: int = 1 << 20, steps: int = 8000, batch: int = 
         E, Y = training_set(sp, n, seed, device=device)
     l2lo, l2hi = log2_range()
     x = scaled_input(E, l2lo, l2hi)
-    mean = Y.mean(0)
-    scale = Y.std(0).clamp(min=1e-3)
-    T = ((Y - mean) / scale).to(torch.float32).contiguous()
+    mean, scale, T = ionize.mlp_standardize(Y.contiguous(), 1e-3)
     P = init_params(Z, seed + 1, device)
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
@@ -129,29 +121,14 @@ def train(sp: ionize.Species, n: int = 1 << 20, steps: int = 8000, batch: int = 
     return Trained(P, norm, losses, steps)
 
 
-def error_bound(sp: ionize.Species, net: ionize.Surrogate, nbins: int = 4096,
-                per_bin: int = 64, margin: float = 1.25, floor_add: float = 2e-3,
-                device="cuda"):
-    """(nbins, Z) bound on |log2 W_net - log2 W| per input bin (both clamped
-    at y_floor), from per_bin points of each bin: the observed maximum
-    times `margin` plus `floor_add`."""
-    l2lo, l2hi = log2_range()
-    j = torch.arange(nbins * per_bin, device=device, dtype=torch.float64)
-    # points at the bin edges and spread inside each bin
-    l2 = l2lo + (l2hi - l2lo) * (torch.floor(j / per_bin) + (j % per_bin) / (per_bin - 1)) / nbins
-    E = torch.exp2(l2).to(torch.float32)
-    Wn = net.rates(E)  # (Z, n)
-    yn = torch.log2(Wn.double()).clamp(min=Y_FLOOR).T
-    yt = plain_log2_rates(sp, E)
-    d = (yn - yt).abs().reshape(nbins, per_bin, sp.Z).amax(1)
-    return (d * margin + floor_add).cpu().numpy().astype(np.float32)
-
-
 def build(sp: ionize.Species, steps: int = 8000, nbins: int = 4096, seed: int = 11,
-          device="cuda", **kw):
-    """Train, bound and create the surrogate: (Surrogate, Trained, bound)."""
+          device="cuda", per_bin: int = 64, margin: float = 1.25, floor_add: float = 2e-3,
+          **kw):
+    """Train, create and validate the surrogate: (Surrogate, Trained, bound),
+    bound the (nbins, Z) array of log2-error bounds it trusts the network by
+    (ion_surrogate_validate: per bin the largest |log2 W_net - log2 W| over
+    per_bin points, times margin, plus floor_add)."""
     tr = train(sp, steps=steps, seed=seed, device=device, **kw)
-    raw = ionize.Surrogate(sp, tr.P, tr.norm, None)
-    bound = error_bound(sp, raw, nbins=nbins, device=device)
-    raw.close()
-    return ionize.Surrogate(sp, tr.P, tr.norm, bound), tr, bound
+    net = ionize.Surrogate(sp, tr.P, tr.norm, None)
+    bound = net.validate(nbins=nbins, per_bin=per_bin, margin=margin, floor_add=floor_add)
+    return net, tr, bound

@@ -70,6 +70,15 @@ def normal(seed: int, stream: int, idx: torch.Tensor) -> torch.Tensor:
     return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
 
 
+def log_uniform_fields(seed: int, stream: int, n: int, log10_lo: float, log10_hi: float,
+                       device="cpu") -> torch.Tensor:
+    """n fields |E| in GV/m with log10|E| uniform in [log10_lo, log10_hi],
+    float32 (the surrogate's training and test inputs)."""
+    idx = torch.arange(n, device=device, dtype=torch.int64)
+    u = uniform(seed, stream, idx)
+    return torch.pow(10.0, log10_lo + (log10_hi - log10_lo) * u).to(torch.float32)
+
+
 # ---------------------------------------------------------------------------
 # species
 # ---------------------------------------------------------------------------
