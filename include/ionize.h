@@ -333,9 +333,10 @@ ION_API int ion_conservation(const void* N, int64_t ld, int64_t ncells, int npla
  * 4-byte aligned; batches hold 1..2^24 samples. */
 #define ION_MLP_HIDDEN 64
 /* Forward pass in the inference arithmetic: W2, W3, h1 and h2 rounded to
- * bf16 and the SFU tanh, as in the tensor-core kernels; the backward pass
- * treats the rounding as the identity (straight-through).  Without it the
- * forward pass is plain FP32 with tanhf. */
+ * bf16 pairs (hi = bf16(v), lo = bf16(v - hi); the value hi + lo) and the
+ * SFU tanh, as in the tensor-core kernels; the backward pass treats the
+ * rounding as the identity (straight-through).  Without it the forward pass
+ * is plain FP32 with tanhf. */
 #define ION_MLP_BF16 0x1
 
 /* Parameter count for K outputs (ION_EINVAL if K is outside 1..ION_MAX_Z). */
@@ -411,11 +412,13 @@ ION_API int ion_mlp_standardize(const double* Y, int64_t n, int K, double min_sc
 
 /* ---- rate surrogate: inference -------------------------------------------
  * A trained network (parameters as above, K = Z outputs) becomes an
- * ion_surrogate: W2 and W3 in bf16 laid out for the tensor cores, the other
- * parameters in FP32.  Its kernels evaluate the network for 128 cells at a
- * time: layer 1 (one input) and the GELUs on the CUDA cores, layers 2 and 3
- * as 128 x 64 x 64 and 128 x N x 64 bf16 products with FP32 accumulation on
- * the tensor cores (tcgen05, accumulators in tensor memory).
+ * ion_surrogate: W2 and W3 as bf16 pairs (hi = bf16(w), lo = bf16(w - hi))
+ * laid out for the tensor cores, the other parameters in FP32.  Its kernels
+ * evaluate the network for 128 cells at a time: layer 1 (one input) and the
+ * GELUs on the CUDA cores, layers 2 and 3 as 128 x 64 x 64 and 128 x N x 64
+ * bf16 products with FP32 accumulation on the tensor cores (tcgen05,
+ * accumulators in tensor memory), the activations as bf16 pairs too, each
+ * product as hi*hi' + hi*lo' + lo*hi' (16 significant bits per operand).
  *
  * Input and output scaling (ion_surrogate_norm):
  *   x = 2 (log2|E| - log2E_min) / (log2E_max - log2E_min) - 1,

@@ -43,6 +43,16 @@ __device__ __forceinline__ float bf16_round(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
 
+// The inference arithmetic carries each value of W2, W3, h1 and h2 as a pair
+// of bf16 numbers, hi = bf16(v) and lo = bf16(v - hi), and the tensor cores
+// sum hi*hi' + hi*lo' + lo*hi' in FP32 (the lo*lo' product, about 2^-16 of
+// the others, is left out).  The pair holds v to about 2^-16 relative;
+// split_round is hi + lo (exact in FP32).
+__device__ __forceinline__ float split_round(float x) {
+  const float hi = bf16_round(x);
+  return hi + bf16_round(x - hi);
+}
+
 // GELU and the tanh it used.  Fast: the SFU tanh (the inference arithmetic);
 // otherwise tanhf.
 template <bool Fast>

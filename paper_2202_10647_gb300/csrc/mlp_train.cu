@@ -13,9 +13,10 @@
 //   mlp_grad_sum    sums the slices in a fixed order (deterministic), and the
 //                   per-block loss partials.
 //   mlp_adam        Adam with bias-corrected moments.
-// With ION_MLP_BF16 the forward pass rounds W2, W3, h1 and h2 to bf16 and
-// takes the SFU tanh, as the tensor-core inference does; the backward pass
-// then treats the rounding as the identity (straight-through).
+// With ION_MLP_BF16 the forward pass rounds W2, W3, h1 and h2 to their
+// bf16 pairs (split_round) and takes the SFU tanh, as the tensor-core
+// inference does; the backward pass then treats the rounding as the identity
+// (straight-through).
 #include <cmath>
 #include <cstdint>
 
@@ -88,11 +89,11 @@ __device__ __forceinline__ void stage(const float* __restrict__ P, int K, Net<KP
   }
   for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
     const float w = P[off_W2() + i];
-    n.W2[i] = Q ? bf16_round(w) : w;
+    n.W2[i] = Q ? split_round(w) : w;
   }
   for (int i = threadIdx.x; i < KP * H; i += blockDim.x) {
     const float w = i < K * H ? P[off_W3() + i] : 0.0f;
-    n.W3[i] = Q ? bf16_round(w) : w;
+    n.W3[i] = Q ? split_round(w) : w;
   }
   for (int k = threadIdx.x; k < KP; k += blockDim.x) n.b3[k] = k < K ? P[off_b3(K) + k] : 0.0f;
 }
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
   for (int i = 0; i < H; ++i) {
     const float h = gelu<Q>(fmaf(n.W1[i], xb, n.b1[i]));
-    h1[i] = Q ? bf16_round(h) : h;
+    h1[i] = Q ? split_round(h) : h;
     if (on) a.h1[(int64_t)b * H + i] = h1[i];
   }
   float y[KP];
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int i = 0; i < H; ++i) z = fmaf(n.W2[o * H + i], h1[i], z);
     float h = gelu<Q>(z);
-    h = Q ? bf16_round(h) : h;
+    h = Q ? split_round(h) : h;
     if (on) {
       a.dz2[(int64_t)bb * H + o] = z;  // z2, overwritten by dL/dz2 later
       a.h2[(int64_t)bb * H + o] = h;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
   for (int i = 0; i < H; ++i) {
     const float h = gelu<Q>(fmaf(n.W1[i], xb, n.b1[i]));
-    h1[i] = Q ? bf16_round(h) : h;
+    h1[i] = Q ? split_round(h) : h;
   }
   float y[KP];
 #pragma unroll
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int i = 0; i < H; ++i) z = fmaf(n.W2[o * H + i], h1[i], z);
     float h = gelu<Q>(z);
-    h = Q ? bf16_round(h) : h;
+    h = Q ? split_round(h) : h;
 #pragma unroll
     for (int k = 0; k < KP; ++k) y[k] = fmaf(n.W3[k * H + o], h, y[k]);
   }

@@ -10,7 +10,7 @@ the tensors, draws the batch order and gathers the batches):
   train          inputs from ion_mlp_inputs, targets standardized per state
                  by ion_mlp_standardize; Adam on the mean squared error
                  (ion_mlp_loss_grad, ion_mlp_adam), the last steps in the
-                 inference arithmetic (bf16, straight-through).
+                 inference arithmetic (bf16 pairs, SFU tanh; straight-through).
   build          train, then ion_surrogate_validate: the tensor-core network
                  against Eq. 1 in FP64 on a dense grid, per input bin and
                  state the largest |log2 W_net - log2 W| (both clamped at
@@ -78,8 +78,8 @@ class Trained:
     steps: int
 
 
-def train(sp: ionize.Species, n: int = 1 << 20, steps: int = 8000, batch: int = 8192,
-          lr: float = 3e-3, lr_end: float = 3e-5, bf16_steps: int = 1500, seed: int = 11,
+def train(sp: ionize.Species, n: int = 1 << 20, steps: int = 40000, batch: int = 8192,
+          lr: float = 1e-2, lr_end: float = 3e-5, bf16_steps: int = 2000, seed: int = 11,
           device="cuda", E=None, Y=None) -> Trained:
     """Adam with a cosine learning-rate schedule from lr to lr_end; the last
     bf16_steps steps use the inference arithmetic."""
@@ -121,7 +121,7 @@ def train(sp: ionize.Species, n: int = 1 << 20, steps: int = 8000, batch: int = 
     return Trained(P, norm, losses, steps)
 
 
-def build(sp: ionize.Species, steps: int = 8000, nbins: int = 4096, seed: int = 11,
+def build(sp: ionize.Species, steps: int = 40000, nbins: int = 4096, seed: int = 11,
           device="cuda", per_bin: int = 64, margin: float = 1.25, floor_add: float = 2e-3,
           **kw):
     """Train, create and validate the surrogate: (Surrogate, Trained, bound),

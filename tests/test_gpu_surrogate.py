@@ -68,10 +68,10 @@ def test_forward_and_adam_match_oracle():
 
 @pytest.mark.parametrize("Z,n", [(7, 1000), (18, 300_000), (36, 4099), (63, 257)])
 def test_tensor_core_inference_matches_cuda_core_forward(Z, n):
-    """The tcgen05 kernel (bf16 operands, FP32 accumulators in tensor memory)
-    against ion_mlp_forward in the same arithmetic on CUDA cores: equal up to
-    the accumulation order (an occasional one-ulp bf16 flip of a hidden
-    activation)."""
+    """The tcgen05 kernel (bf16-pair operands, FP32 accumulators in tensor
+    memory) against ion_mlp_forward in the same arithmetic on CUDA cores:
+    equal up to the accumulation order and the lo*lo' products the tensor
+    cores leave out."""
     sd = W.synthetic_ladder(Z, 90 + Z)
     sp = gpu_species(sd)
     P = torch.tensor(rand_P(Z, Z, 0.3), dtype=torch.float32, device="cuda")
@@ -86,11 +86,14 @@ def test_tensor_core_inference_matches_cuda_core_forward(Z, n):
     x = S.scaled_input(E, l2lo, l2hi)
     y_cc = ionize.mlp_forward(P, Z, x, flags=ionize.ION_MLP_BF16).double()
     d = (y_tc - y_cc).abs()
-    assert float(d.max()) <= 2e-2, float(d.max())
-    assert float(d.median()) <= 1e-5, float(d.median())
-    # against plain FP32 (no bf16): close, not equal
     y32 = ionize.mlp_forward(P, Z, x).double()
-    assert float((y_tc - y32).abs().max()) <= 0.2
+    d32 = (y_tc - y32).abs()
+    print(f"Z={Z}: |tensor cores - CUDA-core inference arithmetic| max {float(d.max()):.2e}, "
+          f"median {float(d.median()):.2e}; against plain FP32 max {float(d32.max()):.2e}")
+    assert float(d.max()) <= 2e-4, float(d.max())
+    assert float(d.median()) <= 1e-5, float(d.median())
+    # against plain FP32 (tanhf, no rounding): the SFU tanh's error only
+    assert float(d32.max()) <= 2e-3
 
 
 def bf16(a):
@@ -102,31 +105,39 @@ def bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def bf16_pair(a):
+    """The value a bf16 pair carries: hi = bf16(a), lo = bf16(a - hi), hi + lo
+    (the rounding of a - hi in float32, as the kernel forms it)."""
+    hi = bf16(a)
+    d = (np.asarray(a, dtype=np.float32).astype(np.float64) - hi).astype(np.float32)
+    return hi + bf16(d)
+
+
 def forward_bf16(P, K, x):
     """The FP64 reference network (oracle/mlp.py) with the tensor-core
-    arithmetic's roundings written in: W2 and W3 as bf16, the hidden
-    activations h1 and h2 rounded to bf16 before each product, the products
-    summed in FP64 (the kernel sums them in FP32)."""
+    arithmetic's roundings written in: W2, W3 and the hidden activations h1
+    and h2 as bf16 pairs (hi + lo) before each product, the products summed
+    in FP64 (the kernel sums hi*hi' + hi*lo' + lo*hi' in FP32)."""
     W1, b1, W2, b2, W3, b3 = omlp.unpack(P, K)
     x = np.asarray(x, dtype=np.float64).reshape(-1)
-    h1 = bf16(omlp.gelu(x[:, None] * W1[None, :] + b1[None, :]))
-    h2 = bf16(omlp.gelu(h1 @ bf16(W2).T + b2[None, :]))
-    return h2 @ bf16(W3).T + b3[None, :]
+    h1 = bf16_pair(omlp.gelu(x[:, None] * W1[None, :] + b1[None, :]))
+    h2 = bf16_pair(omlp.gelu(h1 @ bf16_pair(W2).T + b2[None, :]))
+    return h2 @ bf16_pair(W3).T + b3[None, :]
+
+
+# deviation of the tensor-core outputs from the bf16-pair reference (outputs
+# of order one): per output, at the 99th percentile, in the median (measured
+# on the GB300: at most 4.0e-5, 1.4e-5 and 2.8e-6 over Z = 7, 18, 36, 63)
+TC_MAX, TC_P99, TC_MEDIAN = 2e-4, 5e-5, 1e-5
 
 
 @pytest.mark.parametrize("Z,n", [(7, 4099), (18, 20000), (36, 4099), (63, 1031)])
 def test_tensor_core_network_matches_oracle_with_bf16_rounding(Z, n):
     """The tcgen05 network element by element against the FP64 reference
-    network with bf16 rounding of W2, W3, h1 and h2 written in.  What is left
-    is the SFU tanh of the GELU (tanh.approx.f32) and the FP32 sums: where
-    the approximate tanh moves a hidden activation across a bf16 rounding
-    boundary, that activation differs by one bf16 ulp (2^-7 relative), and
-    the outputs by up to about 1e-2.  A model of the worst case (the
-    reference with its tanh perturbed uniformly by up to 2^-10) deviates by
-    at most 1.9e-2 per output; on the GB300 the deviation is at most 9e-3,
-    3.5e-4 at the 99th percentile and 5e-8 in the median (no flip in most
-    outputs).  Tolerances: 2e-2 per output, 2e-3 at the 99th percentile,
-    1e-6 in the median."""
+    network with the bf16-pair rounding of W2, W3, h1 and h2 written in.
+    What is left is the SFU tanh of the GELU (tanh.approx.f32, relative error
+    up to about 2^-11), the dropped lo*lo' products (about 2^-16 relative)
+    and the FP32 sums."""
     sd = W.synthetic_ladder(Z, 90 + Z)
     sp = gpu_species(sd)
     P32 = torch.tensor(rand_P(Z, 7 * Z, 0.3), dtype=torch.float32)
@@ -145,9 +156,9 @@ def test_tensor_core_network_matches_oracle_with_bf16_rounding(Z, n):
     print(f"Z={Z}: |tensor cores - bf16 reference| max {d.max():.2e}, p99 "
           f"{np.quantile(d, 0.99):.2e}, median {np.median(d):.2e}; against the plain "
           f"FP64 network max {plain.max():.2e}, median {np.median(plain):.2e}")
-    assert d.max() <= 2e-2
-    assert np.quantile(d, 0.99) <= 2e-3
-    assert np.median(d) <= 1e-6
+    assert d.max() <= TC_MAX
+    assert np.quantile(d, 0.99) <= TC_P99
+    assert np.median(d) <= TC_MEDIAN
 
 
 @pytest.fixture(scope="module")
@@ -155,7 +166,7 @@ def argon_net():
     sd = W.argon_like()
     sp = gpu_species(sd)
     t0 = time.time()
-    net, tr, bound = S.build(sp, steps=3000)
+    net, tr, bound = S.build(sp)
     torch.cuda.synchronize()
     print(f"\ntrained in {time.time() - t0:.1f} s; loss {tr.losses[-1]}")
     return sd, sp, net, tr, bound
@@ -165,7 +176,7 @@ def test_trained_network_accuracy(argon_net):
     """The trained network's rates against the oracle's Eq. 1 on fresh
     inputs, and its bound holds there."""
     sd, sp, net, tr, bound = argon_net
-    assert tr.losses[-1][1] < 1e-3, tr.losses
+    assert tr.losses[-1][1] < 1e-4, tr.losses
     n = 20000
     E = torch.pow(10.0, 1.0 + 4.0 * W.uniform(77, 1, torch.arange(n))).to(torch.float32)
     Wn = net.rates(E.cuda()).double().cpu().numpy()
@@ -174,6 +185,9 @@ def test_trained_network_accuracy(argon_net):
     big = Wo * 0.05 > 1e-12
     rel = np.abs(Wn[big] / Wo[big] - 1.0)
     print(f"max rel rate error {rel.max():.3e}, median {np.median(rel):.3e}")
+    # the bf16-pair arithmetic leaves the training error: below 1 % in the
+    # median (single bf16 operands gave about 2 %)
+    assert np.median(rel) < 0.01, np.median(rel)
     l2 = np.log2(E.double().numpy())
     lo, hi = S.log2_range()
     nb = bound.shape[0]
