@@ -580,13 +580,14 @@ def main():
                      "plain_fp32": {"value": n4 / (t_plain4 * 1e-3), "ms_per_step": t_plain4},
                      "gain_vs_plain": t_plain4 / t_net4,
                      "cells": n4, "species": "Ar-like (Z=18)",
-                     "network": "1-64-64-18 GELU, bf16 weights, FP32 accumulation (tcgen05)",
+                     "network": "1-64-64-18 GELU, weights and activations as bf16 pairs, FP32 accumulation (tcgen05)",
                      "train": {"seconds": train_s, "steps": tr4.steps, "pairs": 1 << 20,
                                "final_loss": tr4.losses[-1][1]},
                      "pop_tol": 1e-6,
                      # the network's work per cell: 128 GELUs (one SFU tanh
-                     # each) and 2 (64*64 + 64*Z) bf16 tensor flops (the
-                     # method's Z outputs; the MMA pads them to 32 columns)
+                     # each) and 2 (64*64 + 64*Z) tensor flops of the method
+                     # (its Z outputs; the tensor cores run three bf16
+                     # products per pair and pad the outputs to 32 columns)
                      "roofline": {
                          "bound": "alu",
                          "achieved": 128 * n4 / (t_net4 * 1e-3),
@@ -662,7 +663,7 @@ def main():
             ksur = {"value": 50 * kn / (kres["surrogate_with_check"] * 1e-3),
                     "ms_per_50_steps": kres["surrogate_with_check"],
                     "max_abs_sum_N_minus_1": float(kc.max()),
-                    "network": "1-64-64-36 GELU, bf16 weights, FP32 accumulation (tcgen05)"}
+                    "network": "1-64-64-36 GELU, weights and activations as bf16 pairs, FP32 accumulation (tcgen05)"}
         krypton = {"value": 50 * kn / (kres["with_check"] * 1e-3),
                    "ms_per_50_steps": kres["with_check"],
                    "value_steps_only": 50 * kn / (kres["steps_only"] * 1e-3),
