@@ -306,12 +306,15 @@ __device__ __forceinline__ double log2_rate_f64(const StagedF64& t, int k, const
 //     or at the R that TAU itself needs (FP32).
 // ---------------------------------------------------------------------------
 // Number of Taylor terms: the smallest R with x^(R+1)/(R+1)! below the
-// target (3e-9 in FP32, 2e-17 in FP64), i.e. the number of thresholds
-// kThr[i] = (target (i+1)!)^(1/(i+1)) that lie below x.
+// target, i.e. the number of thresholds kThr[i] = (target (i+1)!)^(1/(i+1))
+// that lie below x.  FP64: target 2e-17.  FP32: target 3e-8 (half an ulp of
+// 1, and 1.5 % of the 2e-6 the FP32 form is held to) for the second and
+// later terms; the first term is taken from x > 3e-9 on, so that no rate
+// whose first-order effect exceeds that is dropped, step after step.
 __device__ constexpr float kThrF32[17] = {
-    3e-09f,    7.74597e-05f, 0.00262074f, 0.0163807f, 0.0514352f, 0.113695f,
-    0.204816f, 0.32384f,     0.46856f,    0.636339f,  0.824531f,  1.03067f,
-    1.25256f,  1.48827f,     1.7361f,     1.99461f,   2.26256f};
+    3e-09f,    0.000244949f, 0.00564622f, 0.0291295f, 0.0815193f, 0.166882f,
+    0.284591f, 0.431847f,    0.605168f,   0.801103f,  1.01652f,   1.24869f,
+    1.49528f,  1.75432f,     2.02414f,    2.30334f,   2.59073f};
 __device__ constexpr double kThrF64[20] = {
     2e-17,     6.32456e-09, 4.93242e-06, 0.000148017, 0.00119136, 0.00493242,
     0.0139108, 0.0307836,   0.0578509,   0.0968455,   0.148911,   0.214675,
@@ -337,9 +340,9 @@ struct DDParams;
 template <>
 struct DDParams<float> {
   static constexpr float tau = 1.0f;   // Taylor below this subset spread
-  static constexpr int RMAX = 11;      // terms needed at spread tau
+  static constexpr int RMAX = 10;      // terms needed at spread tau
   static constexpr float prop_max = 1.0f;  // Taylor propagation up to max W dt
-  static constexpr int PMAX = 16;      // terms needed at 2 * prop_max
+  static constexpr int PMAX = 16;      // bound on the terms (14 needed at 2 * prop_max)
   static constexpr bool kUniform = true;  // every Taylor term up to RMAX
   static constexpr float end_ratio = 4.0f;  // dd_exp_ranges' recurrence bound
   __device__ static __forceinline__ int terms(float x, int rmax) {

@@ -39,7 +39,7 @@ namespace {
 
 constexpr int kStages = 4;
 // The streaming kernel finishes every cell whose rates all have
-// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[16].
+// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[14].
 constexpr float kLamEasy = 1.0f;
 constexpr int kEasyTerms = 16;
 // 1/k! for the Taylor terms of the streaming kernel
@@ -550,18 +550,17 @@ __global__ void __maxnreg__(stream_regs<Q>())
     // Cold chunks: every cell has w < 2 or |E| below the field at which its
     // largest window rate reaches 2^kColdLog2.  The series would take no
     // term (2 W dt <= kThrF32[0]), so the step leaves N as it is and frees
-    // no electron: dne is written, and k_lo/k_hi where the window slides.
-    // (The adaptive policy's rules go the full way.)
+    // no electron: dne is written, and k_lo/k_hi where the window rule
+    // (the paper's slide, or the adaptive rule on the loaded planes) moves
+    // the window.
     bool cold = WMw <= 1;
-    if constexpr (!AD) {
-      if (!cold) {
-        bool c = true;
+    if (!cold) {
+      bool c = true;
 #pragma unroll
-        for (int j = 0; j < Q; ++j)
-          c = c && (!ok[j] || hi[j] == lo[j] ||
-                    fabsf(Ev[j]) < tab.ecold[min(lo[j], ION_MAX_Z)]);
-        cold = __all_sync(kFull, c);
-      }
+      for (int j = 0; j < Q; ++j)
+        c = c && (!ok[j] || hi[j] == lo[j] ||
+                  fabsf(Ev[j]) < tab.ecold[min(lo[j], ION_MAX_Z)]);
+      cold = __all_sync(kFull, c);
     }
     if (cold) {
       float* D = static_cast<float*>(J.dne);
@@ -575,8 +574,21 @@ __global__ void __maxnreg__(stream_regs<Q>())
       for (int j = 0; j < Q; ++j) {
         if (!ok[j]) continue;
         if (!(uni && J.vec)) __stcs(D + c0 + j, 0.0f);
-        if (!AD && (a.pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi[j] > lo[j] &&
-            hi[j] < J.Z && vget(st.P[0][lane], j) < a.pol.eps_f) {
+        if constexpr (AD) {
+          if ((a.pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi[j] > lo[j]) {
+            float v[ION_MAX_WINDOW];
+#pragma unroll
+            for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = vget(st.P[r][lane], j);
+            int nl = lo[j], nh = hi[j];
+            adapt_window<float, ION_MAX_WINDOW>(v, hi[j] - lo[j] + 1, J.Z, a.pol.eps_f,
+                                                a.pol.wmin, a.pol.wmax, a.pol.eps_grow_f, nl, nh);
+            if (nl != lo[j] || nh != hi[j]) {
+              J.lo[c0 + j] = (uint8_t)nl;
+              J.hi[c0 + j] = (uint8_t)nh;
+            }
+          }
+        } else if ((a.pol.flags & ION_NO_WINDOW_UPDATE) == 0 && hi[j] > lo[j] &&
+                   hi[j] < J.Z && vget(st.P[0][lane], j) < a.pol.eps_f) {
           float v[ION_MAX_WINDOW];
 #pragma unroll
           for (int r = 0; r < ION_MAX_WINDOW; ++r) v[r] = vget(st.P[r][lane], j);
