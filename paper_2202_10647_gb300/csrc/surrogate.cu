@@ -2,20 +2,20 @@
 //
 // One CTA of 128 threads owns a tile of 128 cells at a time (thread t <->
 // cell t of the tile <-> row t of the MMAs <-> lane t of tensor memory):
-//   1. each thread evaluates layer 1 of its cell (one input, 64 GELUs) and
+//   1. each thread evaluates layer 1 of its cell (one input, 64 GELUs),
 //      splits h1 into bf16 pairs, hi = bf16(h1) and lo = bf16(h1 - hi) (the
-//      weights are split the same way); the hi parts go into shared memory
-//      in the 128-byte-swizzled K-major layout the tensor cores read;
+//      weights are split the same way), and stores both parts in its lane
+//      of tensor memory (tcgen05.st), where the MMAs read the A operand;
 //   2. one thread issues layer 2 as 12 128x64x16 tcgen05.mma (per 16-wide
-//      slice of K: A_hi W_hi + A_hi W_lo, then, with the lo parts swapped
-//      into the same tile, A_lo W_hi; bf16 in, FP32 accumulators in tensor
-//      memory), committing each group to an mbarrier.  The products carry
-//      16 significant bits of every operand instead of bf16's 8, so the
-//      network's error is its training error rather than bf16 rounding (a
-//      1-64-64-18 network on Ar-like rates: median rate error 0.5 % against
-//      2 % with single bf16 operands);
+//      slice of K: A_hi W_hi + A_hi W_lo + A_lo W_hi; A from tensor memory,
+//      the weights from shared memory, FP32 accumulators in tensor memory)
+//      and commits them to an mbarrier.  The products carry 16 significant
+//      bits of every operand instead of bf16's 8, so the network's error is
+//      its training error rather than bf16 rounding (a 1-64-64-18 network
+//      on Ar-like rates: median rate error 0.5 % against 2 % with single
+//      bf16 operands);
 //   3. every thread reads its row of the accumulators (tcgen05.ld), adds b2,
-//      applies the GELU and writes h2 (hi and lo) over h1;
+//      applies the GELU and stores h2 (hi and lo) over h1;
 //   4. layer 3 likewise (N = the output count padded to 16, 32, 48 or 64),
 //      reusing the same accumulator columns;
 //   5. the outputs, scaled to log2 W, are staged column-major in shared
@@ -46,13 +46,17 @@ namespace sg {
 using mlp::H;
 
 constexpr int kM = 128;            // cells per tile = MMA M = threads per CTA
-constexpr uint32_t kTmemCols = 64; // accumulator columns (layer 3 reuses them)
+// Tensor memory per CTA: columns [0, 64) the accumulators (layer 3 reuses
+// them), [64, 96) the hi parts of the A operand (two bf16 per 32-bit column,
+// the lower K index in the low half), [96, 128) its lo parts.
+constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kColAhi = 64, kColAlo = 96;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Scalars and short vectors of the network and its scaling.
 struct Consts {
-  float W1[H], b1[H], b2[H], b3[64];
-  float ymean[64], yscale[64];
+  float W1h[H], b1h[H], b2h[H];  // W1, b1, b2 halved (the W2 image is halved too)
+  float yoff[64], yscale[64];    // log2 W_k = yscale_k acc_k + yoff_k
   float xa, xb;        // x = xa log2|E| + xb
   float l2lo, l2hi;    // trusted log2|E| range
   float yfloor;        // log2 W below this: W = 0
@@ -169,65 +173,62 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Eight activations as bf16 pairs (mlp::split_round): hi holds bf16(h),
-// lo holds bf16(h - bf16(h)), four packed words each.
-__device__ __forceinline__ void split_pack8(const float (&h)[8], uint4& hi, uint4& lo) {
-  uint32_t H[4], L[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    H[i] = pack_bf16(h[2 * i], h[2 * i + 1]);
-    const float a = __uint_as_float(H[i] << 16), b = __uint_as_float(H[i] & 0xffff0000u);
-    L[i] = pack_bf16(h[2 * i] - a, h[2 * i + 1] - b);
-  }
-  hi = make_uint4(H[0], H[1], H[2], H[3]);
-  lo = make_uint4(L[0], L[1], L[2], L[3]);
+// A pair of activations as bf16 pairs (mlp::split_round): hi holds
+// bf16(a), bf16(b); lo holds the rounded remainders.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16(a, b);
+  lo = pack_bf16(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
-// One layer's products for the 128-row tile, whose A tile holds the hi parts
-// of the activations (the lo parts, four packed words per 8-wide chunk q,
-// wait in lo_pk): A_hi W_hi + A_hi W_lo over the four 16-wide slices of K;
-// once they have read the tile, the lo parts go in its place and A_lo W_hi
-// follows, all into the same accumulator.  One tile instead of two keeps the
-// CTA's shared memory, and so the CTAs per SM, where single bf16 operands
-// had it.  Every thread calls this; thread 0 issues.  Returns false if a
-// bounded wait gave up (the tile is then skipped, and the CTA's drain waits
-// for the commit in flight).  dead_first: the first wait polls `sdead`
-// instead (the test hook of ion_surrogate_test_timeout).
-__device__ __forceinline__ bool layer_pairs(uint32_t tmem, uint32_t sA, uint32_t sBhi,
-                                            uint32_t sBlo, uint32_t idesc, unsigned char* row,
-                                            int t, const uint32_t (&lo_pk)[32], uint32_t sbar,
-                                            uint32_t& phase, bool dead_first, uint32_t sdead) {
+// 8 columns of this thread's lane from 8 registers.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D += A B with A (128 x 16 bf16) read from tensor memory at column a_tmem
+// and B from shared memory.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// One layer's products for the 128-row tile once every thread has stored its
+// row of the A operand (hi and lo parts) in tensor memory: per 16-wide slice
+// kk of K, A_hi W_hi + A_hi W_lo + A_lo W_hi into the accumulators.  Every
+// thread calls this; thread 0 issues.  Returns false if the bounded wait
+// gave up (the tile is then skipped, and the CTA's drain waits for the
+// commit in flight).  dead_first: the wait polls `sdead` instead (the test
+// hook of ion_surrogate_test_timeout).
+__device__ __forceinline__ bool layer_products(uint32_t tmem, uint32_t sBhi, uint32_t sBlo,
+                                               uint32_t idesc, int t, uint32_t sbar,
+                                               uint32_t& phase, bool dead_first,
+                                               uint32_t sdead) {
+  tmem_wait_st();
   tc_fence_before();
-  fence_proxy_async();
   __syncthreads();
   if (t == 0) {
     tc_fence_after();
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-      mma_bf16(tmem, sw128_desc(sA + kk * 32), sw128_desc(sBhi + kk * 32), idesc,
-               kk > 0 ? 1u : 0u);
-      mma_bf16(tmem, sw128_desc(sA + kk * 32), sw128_desc(sBlo + kk * 32), idesc, 1u);
+      const uint32_t ahi = tmem + kColAhi + kk * 8, alo = tmem + kColAlo + kk * 8;
+      mma_bf16_ta(tmem, ahi, sw128_desc(sBhi + kk * 32), idesc, kk > 0 ? 1u : 0u);
+      mma_bf16_ta(tmem, ahi, sw128_desc(sBlo + kk * 32), idesc, 1u);
+      mma_bf16_ta(tmem, alo, sw128_desc(sBhi + kk * 32), idesc, 1u);
     }
     mma_commit(sbar);
   }
-  bool ok = dead_first ? mbar_wait(sdead, 0u, 64u) : mbar_wait(sbar, phase);
-  phase ^= 1u;
-  if (__syncthreads_or(!ok)) return false;
-  // the products have read the tile: the lo parts take its place
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    *reinterpret_cast<uint4*>(row + (((q ^ (t & 7)) & 7) << 4)) =
-        make_uint4(lo_pk[4 * q], lo_pk[4 * q + 1], lo_pk[4 * q + 2], lo_pk[4 * q + 3]);
-  fence_proxy_async();
-  __syncthreads();
-  if (t == 0) {
-    tc_fence_after();
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
-      mma_bf16(tmem, sw128_desc(sA + kk * 32), sw128_desc(sBhi + kk * 32), idesc, 1u);
-    mma_commit(sbar);
-  }
-  ok = mbar_wait(sbar, phase);
+  const bool ok = dead_first ? mbar_wait(sdead, 0u, 64u) : mbar_wait(sbar, phase);
   phase ^= 1u;
   if (__syncthreads_or(!ok)) return false;
   tc_fence_after();
@@ -236,13 +237,13 @@ __device__ __forceinline__ bool layer_pairs(uint32_t tmem, uint32_t sA, uint32_t
 
 // ---- shared-memory plan ---------------------------------------------------
 struct Plan {
-  uint32_t y_bytes;  // A tile (16 KB) / output staging (KP x 128 floats)
+  uint32_t y_bytes;  // output staging (KP x 128 floats)
   uint32_t w2, w3, consts, tab, bar, slot, total;
 };
 
 __host__ __device__ constexpr Plan plan_of(int KP) {
   Plan p{};
-  p.y_bytes = (uint32_t)(KP * 512 > 16384 ? KP * 512 : 16384);
+  p.y_bytes = (uint32_t)(KP * 512);
   p.w2 = p.y_bytes;            // W2 hi, then lo (8 KB each)
   p.w3 = p.w2 + 2 * 8192;      // W3 hi, then lo (KP x 128 bytes each)
   p.consts = p.w3 + 2 * (uint32_t)KP * 128;
@@ -265,23 +266,30 @@ struct StepArgs {
   const float* E;
 };
 
-// Taylor-form update of one cell whose rates all have W dt <= 1 (w <= 6,
+// Taylor-form update of one cell whose rates all have W dt <= 1 (w <= WM,
 // v its window's populations, zero past w): the same series, window slide
-// and stores as ion_step's streaming kernel.
+// and stores as ion_step's streaming kernel.  WM: the warp's width bound.
+template <int WM>
 __device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, int hi,
-                                            float (&v)[ION_MAX_WINDOW],
-                                            const float (&lam)[ION_MAX_WINDOW], float lmax) {
+                                            const float (&v6)[ION_MAX_WINDOW],
+                                            const float (&lam6)[ION_MAX_WINDOW], float lmax) {
   const JobIO& J = a.J;
   float* __restrict__ N = static_cast<float*>(J.N);
   const int w = hi - lo + 1;
   float dne = 0.0f;
   int nlo = lo, nhi = hi;
   if (w >= 2) {
-    dne = taylor_propagate<float, ION_MAX_WINDOW>(v, lam, w, lmax);
-    window_after_step<float, ION_MAX_WINDOW>(J, a.pol, v, w, nlo, nhi);
+    float v[WM], lam[WM];
+#pragma unroll
+    for (int r = 0; r < WM; ++r) {
+      v[r] = v6[r];
+      lam[r] = lam6[r];
+    }
+    dne = taylor_propagate<float, WM>(v, lam, w, lmax);
+    window_after_step<float, WM>(J, a.pol, v, w, nlo, nhi);
     float* q = N + (int64_t)lo * J.ld + c;
 #pragma unroll
-    for (int r = 0; r < ION_MAX_WINDOW; ++r) {
+    for (int r = 0; r < WM; ++r) {
       if (r < w) __stcs(q, v[r]);
       q += J.ld;
     }
@@ -292,6 +300,26 @@ __device__ __forceinline__ void taylor_cell(const StepArgs& a, int c, int lo, in
     J.lo[c] = (uint8_t)nlo;
     J.hi[c] = (uint8_t)nhi;
   }
+}
+
+// The rates of Eq. 1 for the window's w-1 transitions as ion_step's
+// streaming kernel takes them: the plain FP32 exponent for every rate, the
+// float-float recompute for those above 2^-6 (W dt).
+__device__ __forceinline__ void eq1_rates(const StagedF32& tab, int lo, int w, float E,
+                                          float (&lam)[ION_MAX_WINDOW]) {
+  const FieldF32 f = field_f32(E);
+#pragma unroll
+  for (int r = 0; r < ION_MAX_WINDOW - 1; ++r) {
+    if (r < w - 1 && !f.zero) {
+      const float4 h = tab.hi[lo + r];
+      const float q = h.z * f.rE;
+      const float y = (fmaf(-h.y, f.lg, h.x) - q) + h.w;
+      lam[r] = q <= (float)kCutoffLog2 ? ex2_approx(fminf(y, 99.0f)) : 0.0f;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ION_MAX_WINDOW - 1; ++r)
+    if (lam[r] > 1.0f / 64.0f) lam[r] = rate_ff_f32(tab, lo + r, f);
 }
 
 // Counts the lanes with `take` set into *counter (one atomic per warp).
@@ -308,8 +336,7 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
   // align the base to 1024 bytes (the swizzle atoms)
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  unsigned char* A = base;  // A tile, then the output staging Y[k][128]
-  float* Y = reinterpret_cast<float*>(base);
+  float* Y = reinterpret_cast<float*>(base);  // output staging Y[k][128]
   Consts& K = *reinterpret_cast<Consts*>(base + P.consts);
   StagedF32& tab = *reinterpret_cast<StagedF32*>(base + P.tab);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + P.bar);
@@ -352,7 +379,6 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
   tc_fence_after();
   const uint32_t tmem = *slot;
   const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint32_t sA = smem_u32(A);
   const uint32_t sW2 = smem_u32(base + P.w2), sW3 = smem_u32(base + P.w3);
   const uint32_t sbar = smem_u32(bar);
   // Test hook: the first wait of a tile polls, 64 times, a second barrier
@@ -363,7 +389,6 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
   const bool dead_wait = K.dead_wait != 0;
   const int Z = K.Z;
   const float log2dt = (float)a.pol.log2dt;
-  unsigned char* row = A + (t >> 3) * 1024 + (t & 7) * 128;
 
   uint32_t phase = 0;
   bool failed = false;
@@ -407,67 +432,71 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
     // it (field outside the trained range, no rate in the window, or the
     // network never trusted); the decision is uniform over the CTA
     bool use_net = true;
+    // the validation bounds of the window's states, loaded now (like the
+    // populations) so that the loads are in flight during the network
+    float beta[ION_MAX_WINDOW - 1];
+#pragma unroll
+    for (int r = 0; r < ION_MAX_WINDOW - 1; ++r) beta[r] = 0.0f;
     if constexpr (Step) {
       const bool mine = valid && chi > clo && pos && l2 >= K.l2lo && l2 <= K.l2hi &&
                         !a.pol.zero_dt && a.pop_tol > 0.0f;
       use_net = __syncthreads_or(mine) != 0;
+      if (mine && a.bound) {
+        int bin = (int)floorf(fmaf(K.bin_a, l2, K.bin_b));
+        bin = min(max(bin, 0), K.nbins - 1);
+        const float* bb = a.bound + bin * Z + clo;
+#pragma unroll
+        for (int r = 0; r < ION_MAX_WINDOW - 1; ++r)
+          if (r < chi - clo) beta[r] = __ldg(bb + r);
+      }
     }
     if (use_net) {
-    // layer 1 -> A row t, as bf16 pairs: the hi parts into the tile, the lo
-    // parts into registers until layer_pairs swaps them in
-    uint32_t lo_pk[32];
+    // layer 1 -> this thread's row of the A operand in tensor memory, as
+    // bf16 pairs (hi parts from column kColAhi, lo parts from kColAlo), 8
+    // columns (16 activations) at a time
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float h[8];
+    for (int q = 0; q < 4; ++q) {
+      uint32_t hi[8], lo[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = mlp::gelu<true>(fmaf(K.W1[8 * q + j], x, K.b1[8 * q + j]));
-      uint4 hi, lo;
-      split_pack8(h, hi, lo);
-      *reinterpret_cast<uint4*>(row + (((q ^ (t & 7)) & 7) << 4)) = hi;
-      lo_pk[4 * q] = lo.x;
-      lo_pk[4 * q + 1] = lo.y;
-      lo_pk[4 * q + 2] = lo.z;
-      lo_pk[4 * q + 3] = lo.w;
+      for (int j = 0; j < 8; ++j) {
+        const int u = 16 * q + 2 * j;
+        split2(mlp::gelu_half(fmaf(K.W1h[u], x, K.b1h[u])),
+               mlp::gelu_half(fmaf(K.W1h[u + 1], x, K.b1h[u + 1])), hi[j], lo[j]);
+      }
+      tmem_st8(tlane + kColAhi + 8 * q, hi);
+      tmem_st8(tlane + kColAlo + 8 * q, lo);
     }
-    if (!layer_pairs(tmem, sA, sW2, sW2 + 8192, idesc_bf16(kM, H), row, t, lo_pk, sbar, phase,
-                     dead_wait, sdead)) {
+    if (!layer_products(tmem, sW2, sW2 + 8192, idesc_bf16(kM, H), t, sbar, phase, dead_wait,
+                        sdead)) {
       failed = true;
       if (!Step && on)
         for (int k = 0; k < Z; ++k) a.W_out[(int64_t)k * a.ldw + c] = __int_as_float(0x7fc00000);
       continue;
     }
-    // layer 2 epilogue: h2 = g(acc + b2) -> A row t (layer 2 has read A)
+    // layer 2 epilogue: h2 = g(acc + b2) -> the A operand (layer 2 has read
+    // it), 16 accumulator columns at a time
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
       float v[16];
       tmem_ld16(tlane + ch * 16, v);
+      uint32_t hi[8], lo[8];
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float h[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int u = ch * 16 + half * 8 + j;
-          h[j] = mlp::gelu<true>(v[half * 8 + j] + K.b2[u]);
-        }
-        const int q = ch * 2 + half;
-        uint4 hi, lo;
-        split_pack8(h, hi, lo);
-        *reinterpret_cast<uint4*>(row + (((q ^ (t & 7)) & 7) << 4)) = hi;
-        lo_pk[4 * q] = lo.x;
-        lo_pk[4 * q + 1] = lo.y;
-        lo_pk[4 * q + 2] = lo.z;
-        lo_pk[4 * q + 3] = lo.w;
+      for (int j = 0; j < 8; ++j) {
+        const int u = ch * 16 + 2 * j;
+        split2(mlp::gelu_half(v[2 * j] + K.b2h[u]), mlp::gelu_half(v[2 * j + 1] + K.b2h[u + 1]),
+               hi[j], lo[j]);
       }
+      tmem_st8(tlane + kColAhi + 8 * ch, hi);
+      tmem_st8(tlane + kColAlo + 8 * ch, lo);
     }
-    if (!layer_pairs(tmem, sA, sW3, sW3 + KP * 128, idesc_bf16(kM, KP), row, t, lo_pk, sbar,
-                     phase, false, sdead)) {
+    if (!layer_products(tmem, sW3, sW3 + KP * 128, idesc_bf16(kM, KP), t, sbar, phase, false,
+                        sdead)) {
       failed = true;
       if (!Step && on)
         for (int k = 0; k < Z; ++k) a.W_out[(int64_t)k * a.ldw + c] = __int_as_float(0x7fc00000);
       continue;
     }
     // layer 3 epilogue: log2 W_k = ymean + yscale (acc + b3) -> Y[k][t]
-    // (layer 3 has read A, so Y may overwrite it)
 #pragma unroll
     for (int ch = 0; ch < KP / 16; ++ch) {
       float v[16];
@@ -475,7 +504,7 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int k = ch * 16 + j;
-        if (k < Z) Y[k * kM + t] = fmaf(K.yscale[k], v[j] + K.b3[k], K.ymean[k]);
+        if (k < Z) Y[k * kM + t] = fmaf(K.yscale[k], v[j], K.yoff[k]);
       }
     }
     tc_fence_before();
@@ -496,8 +525,6 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
       bool net = false, plain = false;
       if (valid && w >= 2 && !a.pol.zero_dt) {
         const bool in_range = use_net && pos && l2 >= K.l2lo && l2 <= K.l2hi;
-        int bin = (int)floorf(fmaf(K.bin_a, l2, K.bin_b));
-        bin = min(max(bin, 0), K.nbins - 1);
         const float wfloor = exp2f(K.yfloor + log2dt);
         float err = 0.0f;
 #pragma unroll
@@ -506,17 +533,15 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
             const int k = lo + r;
             const float s = Y[k * kM + t];
             lam[r] = s < K.yfloor ? 0.0f : ex2_approx(s + log2dt);
-            const float beta = a.bound ? a.bound[bin * Z + k] : 0.0f;
-            err += 2.0f * fmaf(fmaxf(lam[r], wfloor), beta, wfloor);
+            err += 2.0f * fmaf(fmaxf(lam[r], wfloor), beta[r], wfloor);
           }
         }
         net = in_range && err < a.pop_tol;  // pop_tol 0: never the network
         if (!net) {
           plain = true;
-          const FieldF32 f = field_f32(a.E[c]);
 #pragma unroll
-          for (int r = 0; r < ION_MAX_WINDOW - 1; ++r)
-            if (r < w - 1) lam[r] = rate_dt_f32(tab, lo + r, f);
+          for (int r = 0; r < ION_MAX_WINDOW; ++r) lam[r] = 0.0f;
+          eq1_rates(tab, lo, w, a.E[c], lam);
         }
       }
       // cells with some W dt > 1 take the Bateman form in the record kernel,
@@ -532,7 +557,17 @@ __global__ void __launch_bounds__(kM) surrogate_kernel(const Dev* __restrict__ d
       warp_count(&a.ws.hdr[kHdrPlain], plain);
       if (__ballot_sync(kFull, stiff))
         append_record(a.ws, stiff, 0, (int)c, on ? a.E[c] : 0.0f, lo, hi, v);
-      if (valid && !stiff) taylor_cell(a, (int)c, lo, hi, v, lam, lmax);
+      // the warp's widest window bounds the series for all its lanes
+      const int wt = (valid && !stiff) ? w : 0;
+      const int Wm = __reduce_max_sync(kFull, wt);
+      if (wt > 0) {
+        if (Wm <= 2)
+          taylor_cell<2>(a, (int)c, lo, hi, v, lam, lmax);
+        else if (Wm <= 4)
+          taylor_cell<4>(a, (int)c, lo, hi, v, lam, lmax);
+        else
+          taylor_cell<ION_MAX_WINDOW>(a, (int)c, lo, hi, v, lam, lmax);
+      }
     }
   }
   // leave: tensor memory is freed by the warp that allocated it once every
@@ -787,21 +822,22 @@ int ion_surrogate_create(const ion_species* sp, const float* P, const ion_surrog
     std::memcpy(dst[0] + sg::sw128_offset(r, k), &hi, 2);
     std::memcpy(dst[1] + sg::sw128_offset(r, k), &lo, 2);
   };
+  // W2 halved (exactly), so that layer 2's accumulators arrive halved
   for (int o = 0; o < mlp::H; ++o)
-    for (int k = 0; k < mlp::H; ++k) put(img->W2img, o, k, h[mlp::off_W2() + o * mlp::H + k]);
+    for (int k = 0; k < mlp::H; ++k)
+      put(img->W2img, o, k, 0.5f * h[mlp::off_W2() + o * mlp::H + k]);
   for (int r = 0; r < KP; ++r)
     for (int k = 0; k < mlp::H; ++k)
       put(img->W3img, r, k, r < Z ? h[mlp::off_W3() + r * mlp::H + k] : 0.0f);
   sg::Consts& c = img->k;
   for (int i = 0; i < mlp::H; ++i) {
-    c.W1[i] = h[mlp::off_W1() + i];
-    c.b1[i] = h[mlp::off_b1() + i];
-    c.b2[i] = h[mlp::off_b2() + i];
+    c.W1h[i] = 0.5f * h[mlp::off_W1() + i];
+    c.b1h[i] = 0.5f * h[mlp::off_b1() + i];
+    c.b2h[i] = 0.5f * h[mlp::off_b2() + i];
   }
   for (int k = 0; k < Z; ++k) {
-    c.b3[k] = h[mlp::off_b3(Z) + k];
-    c.ymean[k] = (float)norm->y_mean[k];
     c.yscale[k] = (float)norm->y_scale[k];
+    c.yoff[k] = (float)(norm->y_scale[k] * (double)h[mlp::off_b3(Z) + k] + norm->y_mean[k]);
   }
   const double span = norm->log2E_max - norm->log2E_min;
   c.xa = (float)(2.0 / span);
