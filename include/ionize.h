@@ -209,6 +209,32 @@ ION_API int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld,
              void* dne, const void* n_gas, const ion_step_opts* opts, int flags,
              void* workspace, size_t workspace_bytes, void* stream);
 
+/* ion_field_magnitude -- |E_c| = sqrt(Ex_c^2 + Ey_c^2 + Ez_c^2), the local
+ * field magnitude E_L that Eq. 1 takes (Sec. 2), from the components a
+ * field solver keeps.  Any of Ey, Ez may be
+ * NULL (absent); with Ex alone the result is |Ex|.  Arithmetic in the
+ * dtype (ION_DTYPE_F32: fused multiply-adds and a correctly rounded sqrt;
+ * ION_DTYPE_F64 likewise).
+ *   Ex, Ey, Ez, E_abs  device [ncells] of the dtype, aligned to it.
+ * 0 <= ncells < 2^31.  Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_field_magnitude(const void* Ex, const void* Ey, const void* Ez, int64_t ncells,
+                                int dtype, void* E_abs, void* stream);
+
+/* Workspace bytes of ion_step_field: ion_step's, rounded up to 256, and room
+ * for the magnitudes. */
+ION_API size_t ion_step_field_workspace_bytes(int64_t ncells, int flags);
+
+/* ion_step_field -- ion_step with the field given by its components (Ey, Ez
+ * may be NULL): ion_field_magnitude into the workspace, then ion_step on the
+ * magnitudes (with Ex alone, ion_step on Ex directly: Eq. 1 takes |E|).
+ * Arguments and errors as ion_step; the components have E's dtype and
+ * alignment; workspace >= ion_step_field_workspace_bytes(ncells, flags). */
+ION_API int ion_step_field(const ion_species* sp, const void* Ex, const void* Ey,
+                           const void* Ez, void* N, int64_t ld, int64_t ncells, double dt_fs,
+                           uint8_t* k_lo, uint8_t* k_hi, void* dne, const void* n_gas,
+                           const ion_step_opts* opts, int flags, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
 /* One species' cells for ion_step_batched: the arguments of ion_step that
  * belong to a species.  The jobs of one call must not share cells. */
 typedef struct {

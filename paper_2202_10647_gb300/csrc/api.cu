@@ -121,6 +121,18 @@ __global__ void log2_rates_kernel(const ion::SpeciesTable* t, const float* E, in
   for (int k = k_lo; k < k_hi; ++k) out[c * ldo + (k - k_lo)] = ion::log2_rate_f64(tab, k, f, floor);
 }
 
+template <typename T>
+__global__ void field_magnitude_kernel(const T* Ex, const T* Ey, const T* Ez, int64_t n,
+                                       T* out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const T x = Ex[c];
+  T e2 = x * x;
+  if (Ey) e2 = fma(Ey[c], Ey[c], e2);
+  if (Ez) e2 = fma(Ez[c], Ez[c], e2);
+  out[c] = (Ey || Ez) ? sqrt(e2) : fabs(x);
+}
+
 int check_species(const ion_species* sp) {
   if (!sp || !sp->dev) return fail(ION_EINVAL, "species is NULL or destroyed");
   return ION_OK;
@@ -261,6 +273,39 @@ int ion_log2_rates(const ion_species* sp, const float* E, int64_t ncells, int k_
 size_t ion_step_workspace_bytes(int64_t ncells, int flags) {
   if (ncells < 0) ncells = 0;
   return ion::step_workspace_bytes(ncells, (flags & ION_F64_PLAIN) != 0);
+}
+
+int ion_field_magnitude(const void* Ex, const void* Ey, const void* Ez, int64_t ncells,
+                        int dtype, void* E_abs, void* stream) {
+  if (ncells < 0 || ncells >= (int64_t(1) << 31))
+    return fail(ION_EINVAL, "ncells=%lld outside [0, 2^31)", (long long)ncells);
+  if (dtype != ION_DTYPE_F32 && dtype != ION_DTYPE_F64)
+    return fail(ION_EINVAL, "dtype must be ION_DTYPE_F32 or ION_DTYPE_F64");
+  if (ncells == 0) return ok();
+  if (!Ex || !E_abs) return fail(ION_EINVAL, "Ex and E_abs must be non-NULL");
+  const uintptr_t a = dtype == ION_DTYPE_F32 ? 3u : 7u;
+  for (const void* p : {Ex, Ey, Ez, static_cast<const void*>(E_abs)})
+    if (reinterpret_cast<uintptr_t>(p) & a)
+      return fail(ION_EINVAL, "the field arrays must be aligned to their element size");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned blocks = (unsigned)((ncells + 255) / 256);
+  if (dtype == ION_DTYPE_F32)
+    field_magnitude_kernel<float><<<blocks, 256, 0, s>>>(
+        static_cast<const float*>(Ex), static_cast<const float*>(Ey),
+        static_cast<const float*>(Ez), ncells, static_cast<float*>(E_abs));
+  else
+    field_magnitude_kernel<double><<<blocks, 256, 0, s>>>(
+        static_cast<const double*>(Ex), static_cast<const double*>(Ey),
+        static_cast<const double*>(Ez), ncells, static_cast<double*>(E_abs));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ok() : cuda_fail(e, "ion_field_magnitude launch");
+}
+
+size_t ion_step_field_workspace_bytes(int64_t ncells, int flags) {
+  if (ncells < 0) ncells = 0;
+  const size_t elem = (flags & ION_F64_PLAIN) ? 8 : 4;
+  const size_t step = (ion_step_workspace_bytes(ncells, flags) + 255) / 256 * 256;
+  return step + ((size_t)ncells * elem + 255) / 256 * 256;
 }
 
 }  // extern "C"
@@ -453,6 +498,31 @@ int ion_step(const ion_species* sp, const void* E, void* N, int64_t ld, int64_t 
   if (rc) return rc;
   const ion_batch_job job = {sp, E, N, ld, ncells, k_lo, k_hi, dne, n_gas};
   return run_batch(&job, 1, dt_fs, opts, flags, nullptr, workspace, workspace_bytes, stream);
+}
+
+int ion_step_field(const ion_species* sp, const void* Ex, const void* Ey, const void* Ez,
+                   void* N, int64_t ld, int64_t ncells, double dt_fs, uint8_t* k_lo,
+                   uint8_t* k_hi, void* dne, const void* n_gas, const ion_step_opts* opts,
+                   int flags, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_species(sp);
+  if (rc) return rc;
+  if (!Ey && !Ez)
+    return ion_step(sp, Ex, N, ld, ncells, dt_fs, k_lo, k_hi, dne, n_gas, opts, flags,
+                    workspace, workspace_bytes, stream);
+  if (ncells < 0 || ncells >= (int64_t(1) << 31))
+    return fail(ION_EINVAL, "ncells=%lld outside [0, 2^31)", (long long)ncells);
+  const size_t need = ion_step_field_workspace_bytes(ncells, flags);
+  if (!workspace || workspace_bytes < need)
+    return fail(ION_EINVAL, "workspace: %zu bytes given, %zu needed", workspace_bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+    return fail(ION_EINVAL, "workspace must be 256-byte aligned");
+  const size_t step = (ion_step_workspace_bytes(ncells, flags) + 255) / 256 * 256;
+  void* Emag = static_cast<char*>(workspace) + step;
+  rc = ion_field_magnitude(Ex, Ey, Ez, ncells,
+                           (flags & ION_F64_PLAIN) ? ION_DTYPE_F64 : ION_DTYPE_F32, Emag, stream);
+  if (rc) return rc;
+  return ion_step(sp, Emag, N, ld, ncells, dt_fs, k_lo, k_hi, dne, n_gas, opts, flags,
+                  workspace, step, stream);
 }
 
 int ion_step_batched(const ion_batch_job* jobs, int njobs, double dt_fs,

@@ -36,7 +36,8 @@ ION_MAX_WINDOW = 6
 
 #: every symbol include/ionize.h declares
 EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
-           "ion_rates", "ion_step_workspace_bytes", "ion_step",
+           "ion_rates", "ion_step_workspace_bytes", "ion_step", "ion_field_magnitude",
+           "ion_step_field_workspace_bytes", "ion_step_field",
            "ion_step_batched_workspace_bytes", "ion_step_batched", "ion_autotune",
            "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
            "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
@@ -47,7 +48,7 @@ EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_binary_version",
            "ion_last_error")
 
-#: forward pass in the tensor-core arithmetic (bf16 W2, W3, h1, h2; SFU tanh)
+#: forward pass in the tensor-core arithmetic (W2, W3, h1, h2 as bf16 pairs; SFU tanh)
 ION_MLP_BF16 = 0x1
 ION_MLP_HIDDEN = 64
 
@@ -175,6 +176,13 @@ def _declare(lib):
                                  ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp]
     lib.ion_mlp_forward.restype = ctypes.c_int
     lib.ion_mlp_forward.argtypes = [_vp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]
+    lib.ion_field_magnitude.restype = ctypes.c_int
+    lib.ion_field_magnitude.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp]
+    lib.ion_step_field_workspace_bytes.restype = ctypes.c_size_t
+    lib.ion_step_field_workspace_bytes.argtypes = [_i64, ctypes.c_int]
+    lib.ion_step_field.restype = ctypes.c_int
+    lib.ion_step_field.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _i64, ctypes.c_double, _vp,
+                                   _vp, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]
     lib.ion_log2_rates.restype = ctypes.c_int
     lib.ion_log2_rates.argtypes = [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                    _vp, _i64, _vp]
@@ -317,6 +325,67 @@ def rates(sp: Species, E: torch.Tensor, k_lo: int, k_hi: int,
     _check(lib().ion_rates(sp.handle, _ptr(E), n, int(k_lo), int(k_hi), _ptr(out),
                            ldw, dtype, _stream(E)))
     return out
+
+
+def field_magnitude(Ex: torch.Tensor, Ey: torch.Tensor | None = None,
+                    Ez: torch.Tensor | None = None,
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+    """ion_field_magnitude: |E| from 1-3 components (float32 or float64)."""
+    if Ex.dtype not in (torch.float32, torch.float64):
+        raise ValueError("Ex must be float32 or float64")
+    _need(Ex, "Ex", Ex.dtype)
+    for name, t in (("Ey", Ey), ("Ez", Ez)):
+        if t is not None:
+            _need(t, name, Ex.dtype, Ex.device)
+            if t.numel() < Ex.numel():
+                raise ValueError(f"{name} is shorter than Ex")
+    out = torch.empty_like(Ex) if out is None else out
+    _need(out, "out", Ex.dtype, Ex.device)
+    dtype = ION_DTYPE_F32 if Ex.dtype == torch.float32 else ION_DTYPE_F64
+    _check(lib().ion_field_magnitude(_ptr(Ex), _ptr(Ey), _ptr(Ez), Ex.numel(), dtype, _ptr(out),
+                                     _stream(Ex)))
+    return out
+
+
+def step_field(sp: "Species", components, N: torch.Tensor, k_lo: torch.Tensor,
+               k_hi: torch.Tensor, dt: float, dne: torch.Tensor,
+               n_gas: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+               eps_shift: float = 1e-6, degen_gap: float = 1e-3, flags: int = ION_F32,
+               window: dict | None = None) -> torch.Tensor:
+    """ion_step_field: ion_step with the field as 1-3 component tensors
+    (Ex, Ey, Ez; missing ones None or left out).  Returns the workspace."""
+    comps = list(components) + [None] * (3 - len(components))
+    Ex, Ey, Ez = comps[:3]
+    f64 = bool(flags & ION_F64_PLAIN)
+    dt_ = torch.float64 if f64 else torch.float32
+    _need(Ex, "Ex", dt_)
+    dev = Ex.device
+    n = Ex.numel()
+    for name, t in (("Ey", Ey), ("Ez", Ez)):
+        if t is not None:
+            _need(t, name, dt_, dev)
+            if t.numel() < n:
+                raise ValueError(f"{name} is shorter than Ex")
+    _need(N, "N", dt_, dev)
+    _need(k_lo, "k_lo", torch.uint8, dev)
+    _need(k_hi, "k_hi", torch.uint8, dev)
+    _need(dne, "dne", dt_, dev)
+    if n_gas is not None:
+        _need(n_gas, "n_gas", dt_, dev)
+    if N.dim() != 2 or N.shape[0] != sp.Z + 1:
+        raise ValueError(f"N must have shape (Z+1, ld) = ({sp.Z + 1}, ld)")
+    if n > min(k_lo.numel(), k_hi.numel(), dne.numel(), N.shape[1]):
+        raise ValueError("the arrays are shorter than Ex")
+    if ws is None:
+        nb = int(lib().ion_step_field_workspace_bytes(n, int(flags)))
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    _need(ws, "ws", torch.uint8, dev)
+    opts = _opts(eps_shift, degen_gap, window)
+    _check(lib().ion_step_field(sp.handle, _ptr(Ex), _ptr(Ey), _ptr(Ez), _ptr(N), N.shape[1], n,
+                                float(dt), _ptr(k_lo), _ptr(k_hi), _ptr(dne), _ptr(n_gas),
+                                ctypes.byref(opts), int(flags), _ptr(ws), ws.numel(),
+                                _stream(Ex)))
+    return ws
 
 
 def workspace_bytes(ncells: int, flags: int = ION_F32) -> int:
