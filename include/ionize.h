@@ -193,10 +193,7 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *          untouched because their window was invalid (lo > hi, hi > Z or
  *          w > ION_MAX_WINDOW), word 2 the cells that had a rate with
  *          W dt > 1 (finished by the record kernel in the Bateman form),
- *          word 9 (FP32, paper's window rule, |E|, k_lo and k_hi 16-byte
- *          aligned) the cells some window rate could change (the others
- *          have every window rate below W dt = 2^-30 and keep N), and with
- *          ION_CONSERVATION_CHECK word 10 the bits of a float, the largest
+ *          and with ION_CONSERVATION_CHECK word 10 the bits of a float, the largest
  *          |sum_k N'_k - sum_k N_k| over the cells (the states outside a
  *          window are not touched, so this is the step's whole conservation
  *          error; 0 for cells that do not change, NaN if a sum is NaN).

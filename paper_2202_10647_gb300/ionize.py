@@ -548,14 +548,6 @@ def stiff_cells(ws: torch.Tensor) -> int:
     return int(ws[8:12].cpu().view(torch.int32)[0])
 
 
-def changing_cells(ws: torch.Tensor) -> int:
-    """Cells of the last FP32 step under the paper's window rule (16-byte
-    aligned |E|, k_lo, k_hi) that some window rate could change: the others
-    have every window rate below W dt = 2^-30 and keep their populations;
-    synchronizes."""
-    return int(ws[36:40].cpu().view(torch.int32)[0])
-
-
 def conservation_change(ws: torch.Tensor) -> float:
     """With ION_CONSERVATION_CHECK: the largest |sum_k N'_k - sum_k N_k| over
     the cells of the last step that used `ws` (synchronizes)."""
