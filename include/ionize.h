@@ -342,6 +342,21 @@ ION_API int ion_step_noalloc(const ion_species* sp, const void* E, void* N,
 ION_API int ion_conservation(const void* N, int64_t ld, int64_t ncells, int nplanes,
                              double target, int dtype, float* out_max, void* stream);
 
+/* ion_copy_cells -- the cells [offset, offset + ncells) of `nplanes` plane
+ * rows of one SoA array (rows ld_src elements apart) into another (rows
+ * ld_dst apart), in one strided copy (cudaMemcpy2DAsync, direction from the
+ * pointers); a PIC code moving a range of cells between host and device
+ * (or between two device arrays) issues one call per array instead of one
+ * per plane.  The paper has no counterpart.
+ *   dst, src  device or host (pinned host memory for the copy to run
+ *             asynchronously) arrays of elem_bytes-sized elements.
+ *   elem_bytes 1, 2, 4 or 8; nplanes >= 1; ncells, offset >= 0;
+ *   offset + ncells <= min(ld_dst, ld_src).
+ * Enqueues on `stream`; allocates nothing.  Errors: ION_EINVAL, ION_ECUDA. */
+ION_API int ion_copy_cells(void* dst, int64_t ld_dst, const void* src, int64_t ld_src,
+                           int nplanes, int64_t offset, int64_t ncells, int elem_bytes,
+                           void* stream);
+
 /* ---- rate surrogate: network and training --------------------------------
  * A small network maps the field magnitude to the logarithms of all Z rates
  * of a species at once (the paper evaluates Eq. 1 directly; the surrogate is

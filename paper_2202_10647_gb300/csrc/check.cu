@@ -167,3 +167,26 @@ extern "C" int ion_conservation(const void* N, int64_t ld, int64_t ncells, int n
     return ion::set_error(ION_ECUDA, "ion_conservation launch: %s", cudaGetErrorString(e));
   return ion::set_error(ION_OK, "%s", "");
 }
+
+extern "C" int ion_copy_cells(void* dst, int64_t ld_dst, const void* src, int64_t ld_src,
+                              int nplanes, int64_t offset, int64_t ncells, int elem_bytes,
+                              void* stream) {
+  if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8)
+    return ion::set_error(ION_EINVAL, "ion_copy_cells: elem_bytes=%d not 1, 2, 4 or 8",
+                          elem_bytes);
+  if (nplanes < 1 || ncells < 0 || offset < 0)
+    return ion::set_error(ION_EINVAL, "ion_copy_cells: need nplanes >= 1, ncells >= 0, "
+                                      "offset >= 0");
+  if (ncells == 0) return ion::set_error(ION_OK, "%s", "");
+  if (!dst || !src) return ion::set_error(ION_EINVAL, "ion_copy_cells: NULL array");
+  if (offset + ncells > ld_dst || offset + ncells > ld_src)
+    return ion::set_error(ION_EINVAL, "ion_copy_cells: offset + ncells exceeds a row");
+  const size_t eb = (size_t)elem_bytes;
+  const cudaError_t e = cudaMemcpy2DAsync(
+      static_cast<char*>(dst) + offset * eb, (size_t)ld_dst * eb,
+      static_cast<const char*>(src) + offset * eb, (size_t)ld_src * eb, (size_t)ncells * eb,
+      (size_t)nplanes, cudaMemcpyDefault, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess)
+    return ion::set_error(ION_ECUDA, "ion_copy_cells: %s", cudaGetErrorString(e));
+  return ion::set_error(ION_OK, "%s", "");
+}

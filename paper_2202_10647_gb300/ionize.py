@@ -39,7 +39,7 @@ EXPORTS = ("ion_species_init", "ion_species_destroy", "ion_species_z",
            "ion_rates", "ion_step_workspace_bytes", "ion_step", "ion_field_magnitude",
            "ion_step_field_workspace_bytes", "ion_step_field",
            "ion_step_batched_workspace_bytes", "ion_step_batched", "ion_autotune",
-           "ion_step_noalloc", "ion_conservation", "ion_mlp_nparams",
+           "ion_step_noalloc", "ion_conservation", "ion_copy_cells", "ion_mlp_nparams",
            "ion_mlp_workspace_bytes", "ion_mlp_loss_grad", "ion_mlp_adam", "ion_mlp_forward",
            "ion_log2_rates", "ion_mlp_inputs", "ion_mlp_standardize",
            "ion_surrogate_create", "ion_surrogate_destroy", "ion_surrogate_rates",
@@ -176,6 +176,9 @@ def _declare(lib):
                                  ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp]
     lib.ion_mlp_forward.restype = ctypes.c_int
     lib.ion_mlp_forward.argtypes = [_vp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]
+    lib.ion_copy_cells.restype = ctypes.c_int
+    lib.ion_copy_cells.argtypes = [_vp, _i64, _vp, _i64, ctypes.c_int, _i64, _i64, ctypes.c_int,
+                                   _vp]
     lib.ion_field_magnitude.restype = ctypes.c_int
     lib.ion_field_magnitude.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp]
     lib.ion_step_field_workspace_bytes.restype = ctypes.c_size_t
@@ -325,6 +328,33 @@ def rates(sp: Species, E: torch.Tensor, k_lo: int, k_hi: int,
     _check(lib().ion_rates(sp.handle, _ptr(E), n, int(k_lo), int(k_hi), _ptr(out),
                            ldw, dtype, _stream(E)))
     return out
+
+
+def copy_cells(dst: torch.Tensor, src: torch.Tensor, offset: int, ncells: int) -> None:
+    """ion_copy_cells: cells [offset, offset + ncells) of every row of src
+    (a 1-D array or a (planes, ld) SoA) into the same cells of dst, in one
+    strided copy on the current stream of whichever tensor is on the GPU
+    (host tensors should be pinned)."""
+    if dst.dtype != src.dtype:
+        raise ValueError("dst and src must have the same dtype")
+    if dst.dim() != src.dim() or dst.dim() not in (1, 2):
+        raise ValueError("dst and src must both be 1-D or both (planes, ld)")
+    for name, t in (("dst", dst), ("src", src)):
+        if t.stride(-1) != 1:
+            raise ValueError(f"{name} rows must be contiguous")
+    planes = 1 if dst.dim() == 1 else dst.shape[0]
+    if dst.dim() == 2 and src.shape[0] != planes:
+        raise ValueError("dst and src must have the same number of planes")
+    ld_d = dst.shape[-1] if dst.dim() == 1 else dst.stride(0)
+    ld_s = src.shape[-1] if src.dim() == 1 else src.stride(0)
+    if offset < 0 or ncells < 0 or offset + ncells > min(dst.shape[-1], src.shape[-1]):
+        raise ValueError("offset/ncells outside the arrays")
+    dev = dst.device if dst.is_cuda else src.device
+    if not dev.type == "cuda":
+        raise ValueError("one of dst and src must be a CUDA tensor")
+    _check(lib().ion_copy_cells(ctypes.c_void_p(dst.data_ptr()), ld_d,
+                                ctypes.c_void_p(src.data_ptr()), ld_s, planes, int(offset),
+                                int(ncells), dst.element_size(), _stream_of(dev)))
 
 
 def field_magnitude(Ex: torch.Tensor, Ey: torch.Tensor | None = None,

@@ -87,3 +87,30 @@ def test_step_field_arguments():
         ionize.step_field(sp, [Ex, Ex], N, lo, hi, 0.05, dne, ws=small)
     with pytest.raises(ValueError):
         ionize.field_magnitude(Ex, Ex.double())
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64, torch.uint8])
+def test_copy_cells(dtype):
+    """ion_copy_cells: a cell range of every plane, host to device and back,
+    equal to the same slices copied plane by plane."""
+    Z1, ld = 5, 1000
+    g = torch.Generator().manual_seed(3)
+    src = (torch.rand((Z1, ld), generator=g) * 200).to(dtype).pin_memory()
+    dev = torch.zeros((Z1, ld + 24), dtype=dtype, device="cuda")[:, :ld]  # rows ld + 24 apart
+    ionize.copy_cells(dev, src, 130, 517)
+    torch.cuda.synchronize()
+    want = torch.zeros((Z1, ld), dtype=dtype)
+    want[:, 130:647] = src[:, 130:647]
+    assert torch.equal(dev.cpu(), want)
+    back = torch.full((Z1, ld), 7, dtype=dtype).pin_memory()
+    ionize.copy_cells(back, dev, 100, 600)
+    torch.cuda.synchronize()
+    want2 = torch.full((Z1, ld), 7, dtype=dtype)
+    want2[:, 100:700] = want[:, 100:700]
+    assert torch.equal(back, want2)
+    one = torch.zeros(ld, dtype=dtype, device="cuda")
+    ionize.copy_cells(one, src[2].contiguous().pin_memory(), 0, ld)
+    torch.cuda.synchronize()
+    assert torch.equal(one.cpu(), src[2])
+    with pytest.raises(ValueError):
+        ionize.copy_cells(dev, src, 900, 200)
