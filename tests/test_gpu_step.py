@@ -736,3 +736,17 @@ def test_close_ends_far_inner_node(name):
         err = np.abs(out["N"][:, :n] - ref["N"]).max(axis=0)
         print(f"{name} flags {flags:#x}: {n} cells, {far} stiff with an end-gap ratio "
               f"above 16 (largest {ratio.max():.3g}); max |N - oracle| {err.max():.2e}")
+
+
+def test_fp64_coefficients_for_many_cells():
+    """ION_FORCE_FP64_COEF on 400,000 Ar-like cells: every stiff cell (about
+    64,000, more than one pass of the FP64-coefficient kernel's warps) takes
+    FP64 coefficients, and every cell matches the oracle."""
+    sd = W.argon_like()
+    wl = W.ladder_cells(sd, 400_000, 41)
+    E, N, lo, hi = cells_of(wl)
+    out, ref = run_both(sd, E, N, lo, hi, flags=ionize.ION_F32 | ionize.ION_FORCE_FP64_COEF)
+    check(out, ref, lo, hi, ionize.ION_F32)
+    fb, bad = out["counters"]
+    assert bad == 0
+    assert fb > 40_000, fb
