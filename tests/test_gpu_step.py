@@ -750,3 +750,38 @@ def test_fp64_coefficients_for_many_cells():
     fb, bad = out["counters"]
     assert bad == 0
     assert fb > 40_000, fb
+
+
+@pytest.mark.parametrize("Z", [1, 2, 63])
+@pytest.mark.parametrize("flags", [ionize.ION_F32, ionize.ION_F64_PLAIN])
+def test_smallest_and_largest_species(Z, flags):
+    """Species of 1, 2 and ION_MAX_Z = 63 transitions (synthetic ladders):
+    every window width at the bottom, middle and top of the ladder against
+    fields from 0 to 1e6 GV/m and rate crossings, in both forms."""
+    assert Z <= ionize.ION_MAX_Z
+    sd = W.synthetic_ladder(Z, 60 + Z)
+    E, N, lo, hi = adversarial(sd, seed=Z)
+    out, ref = run_both(sd, E, N, lo, hi, flags=flags)
+    check(out, ref, lo, hi, flags)
+    assert out["counters"][1] == 0
+
+
+def test_batched_smallest_with_largest_species():
+    """One batched launch over a 1-transition and a 63-transition species:
+    each job matches its own oracle step."""
+    jobs, refs = [], []
+    for Z in (1, 63):
+        sd = W.synthetic_ladder(Z, 70 + Z)
+        E, N, lo, hi = adversarial(sd, seed=Z + 1)
+        n = E.numel()
+        No, loo, hio, dneo = oracle.step(oracle_species(sd), E.double().numpy(),
+                                         N[:, :n].double().numpy(), 0.05, lo.numpy(), hi.numpy())
+        jobs.append((gpu_species(sd), E.cuda(), N.cuda(), lo.clone().cuda(), hi.clone().cuda(),
+                     torch.zeros(n, device="cuda")))
+        refs.append((sd, E, lo, hi, dict(N=No, lo=loo, hi=hio, dne=dneo)))
+    ionize.step_batched(jobs, 0.05)
+    torch.cuda.synchronize()
+    for (sp, Eg, Ng, log, hig, dne), (sd, E, lo, hi, ref) in zip(jobs, refs):
+        out = dict(N=Ng.double().cpu().numpy(), lo=log.cpu().numpy(), hi=hig.cpu().numpy(),
+                   dne=dne.double().cpu().numpy(), sd=sd, E=E.double().numpy())
+        check(out, ref, lo, hi, ionize.ION_F32)
