@@ -306,6 +306,8 @@ def summary_of(line):
     if s:
         out["surrogate_argon"] = {"ms": _r(s["ms_per_step"]),
                                   "plain_ms": _r(s["plain_fp32"]["ms_per_step"]),
+                                  "plain_tuned_ms": _r((s.get("plain_fp32_autotuned") or {}).get(
+                                      "ms_per_step")),
                                   "gain": _r(s["gain_vs_plain"], 3),
                                   "on_network": _r(s["cells_on_network_rates"], 3),
                                   "rate_err_median": _r((s.get("accuracy") or {}).get(
@@ -553,6 +555,11 @@ def main():
         t_plain4 = t4(lambda: ionize.step(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4),
                       reps4)
         t_net4 = t4(lambda: net4.step(wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4), reps4)
+        # the same plain step with the launch shape the library's autotuner
+        # picks for these cells (the autotuner steps the arrays: restored by t4)
+        job4 = [(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, dne4)]
+        shape4, _ = ionize.autotune(job4, 0.05, ws=ws4, reps=3)
+        t_tuned4 = t4(lambda: ionize.step_batched(job4, 0.05, ws=ws4, shape=shape4), reps4)
         n_net4, n_plain4, tmo4 = ionize.surrogate_counters(ws4)
         acc4 = None
         if rank == 0:
@@ -580,6 +587,10 @@ def main():
                     "max_abs_err_N_vs_oracle_plain_fp32": float(np.abs(Npl - No4).max())}
         surrogate = {"value": n4 / (t_net4 * 1e-3), "ms_per_step": t_net4,
                      "plain_fp32": {"value": n4 / (t_plain4 * 1e-3), "ms_per_step": t_plain4},
+                     "plain_fp32_autotuned": {
+                         "value": n4 / (t_tuned4 * 1e-3), "ms_per_step": t_tuned4,
+                         "shape": [shape4.cells_per_lane, shape4.warps_per_block,
+                                   shape4.blocks_per_sm]},
                      "gain_vs_plain": t_plain4 / t_net4,
                      "cells": n4, "species": "Ar-like (Z=18)",
                      "network": "1-64-64-18 GELU, weights and activations as bf16 pairs, FP32 accumulation (tcgen05)",

@@ -152,8 +152,9 @@ ION_API int ion_rates(const ion_species* sp, const void* E, int64_t ncells, int 
 /* Bytes of device workspace ion_step needs for `ncells` cells with `flags`:
  * a 256-byte header plus, for ION_F32, 40 bytes per cell: a 5-byte queue
  * slot (cells whose Bateman coefficients are computed in FP64) and a 35-byte
- * record (cells with a rate W dt > 1, finished by the record kernel from the
- * inputs already loaded). */
+ * record (cells with a rate W dt > 1, or > 1.5 under a launch shape of one
+ * cell per lane, finished by the record kernel from the inputs already
+ * loaded). */
 ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
 
 /* ion_step -- advance the charge-state populations of every cell by one
@@ -192,7 +193,8 @@ ION_API size_t ion_step_workspace_bytes(int64_t ncells, int flags);
  *          whose coefficients were computed in FP64, word 1 the cells left
  *          untouched because their window was invalid (lo > hi, hi > Z or
  *          w > ION_MAX_WINDOW), word 2 the cells that had a rate with
- *          W dt > 1 (finished by the record kernel in the Bateman form),
+ *          W dt > 1 (> 1.5 with one cell per lane; finished by the
+ *          record kernel in the Bateman form),
  *          and with ION_CONSERVATION_CHECK word 10 the bits of a float, the largest
  *          |sum_k N'_k - sum_k N_k| over the cells (the states outside a
  *          window are not touched, so this is the step's whole conservation

@@ -311,10 +311,11 @@ __device__ __forceinline__ double log2_rate_f64(const StagedF64& t, int k, const
 // 1, and 1.5 % of the 2e-6 the FP32 form is held to) for the second and
 // later terms; the first term is taken from x > 3e-9 on, so that no rate
 // whose first-order effect exceeds that is dropped, step after step.
-__device__ constexpr float kThrF32[17] = {
+__device__ constexpr float kThrF32[19] = {
     3e-09f,    0.000244949f, 0.00564622f, 0.0291295f, 0.0815193f, 0.166882f,
     0.284591f, 0.431847f,    0.605168f,   0.801103f,  1.01652f,   1.24869f,
-    1.49528f,  1.75432f,     2.02414f,    2.30334f,   2.59073f};
+    1.49528f,  1.75432f,     2.02414f,    2.30334f,   2.59073f,   2.88531f,
+    3.18621f};
 __device__ constexpr double kThrF64[20] = {
     2e-17,     6.32456e-09, 4.93242e-06, 0.000148017, 0.00119136, 0.00493242,
     0.0139108, 0.0307836,   0.0578509,   0.0968455,   0.148911,   0.214675,

@@ -11,8 +11,8 @@
 //       loads in flight cost no registers and the traffic is exactly the
 //       cells' windows.  A chunk whose cells all lie below their species'
 //       cold field (no rate reaches the first Taylor term) only writes dne.
-//       A cell whose rates all have W dt <= 1 is finished
-//       here with the Taylor series of exp(dt A).  The others ("stiff" cells,
+//       A cell whose rates all have W dt <= 1 (1.5 with one cell per
+//       lane) is finished here with the Taylor series of exp(dt A).  The others ("stiff" cells,
 //       the Bateman form) write the inputs already loaded into a record queue:
 //       in a laser field |E| swings from zero to its peak every few cells, so
 //       most warps near the pulse hold a few stiff cells, and finishing them
@@ -39,11 +39,21 @@ namespace {
 
 constexpr int kStages = 4;
 // The streaming kernel finishes every cell whose rates all have
-// W dt <= kLamEasy with the Taylor form; 2 kLamEasy <= kThrF32[14].
-constexpr float kLamEasy = 1.0f;
-constexpr int kEasyTerms = 16;
-// 1/k! for the Taylor terms of the streaming kernel
-__device__ constexpr float kInvFactF32[kEasyTerms + 1] = {
+// W dt <= lam_easy<Q>() with the Taylor form, in at most kEasyTerms terms:
+// 2 lam_easy <= kThrF32[kEasyTerms] (3 <= 3.19).  The warp runs the term
+// count of its largest rate, so the bound trades a longer series for every
+// cell of a warp against the records that a lower bound makes: with 32 cells
+// per warp (Q = 1) the series up to W dt = 1.5 measured faster than records
+// (2-3 % on the Ar-like and mixed batches, the FP32 rounding of the series
+// about 2.7e-7 there against 2.0e-7 at 1); with 64 (Q = 2) records above 1.
+template <int Q>
+constexpr float lam_easy() {
+  return Q == 1 ? 1.5f : 1.0f;
+}
+constexpr int kEasyTerms = 18;
+// 1/k! for the Taylor terms of the streaming kernel (constant memory: the
+// term loop reads one entry per term at a warp-uniform index)
+__constant__ const float kInvFactF32[kEasyTerms + 1] = {
     1.0f,
     1.0f,
     1.0f / 2,
@@ -60,7 +70,9 @@ __device__ constexpr float kInvFactF32[kEasyTerms + 1] = {
     1.0f / 6227020800.0f,
     1.0f / 87178291200.0f,
     1.0f / 1307674368000.0f,
-    1.0f / 20922789888000.0f};
+    1.0f / 20922789888000.0f,
+    1.0f / 355687428096000.0f,
+    1.0f / 6402373705728000.0f};
 // Rates with W dt above this are recomputed in float-float arithmetic.
 constexpr float kLamPrecise = 1.0f / 64.0f;
 
@@ -133,7 +145,7 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 
 // Easy path of the lane's Q cells (c0..c0+Q-1 of job J, window bound WM).
 // Every lane of the warp calls this.  Cells whose rates all have
-// W dt <= kLamEasy are finished; stiff[j] marks the others, left untouched.
+// W dt <= lam_easy<Q>() are finished; stiff[j] marks the others, left untouched.
 // Every window rate first takes the plain FP32 exponent y = (a_hi + a_lo) -
 // b log2|E| - C/|E|: its error is below ~6e-5 in log2 units even for terms of
 // 10^3, i.e. a relative error of W dt below 4e-5, which moves populations by
@@ -188,7 +200,7 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
     float lmax = 0.0f;
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r) lmax = fmaxf(lmax, lam[j][r]);
-    stiff[j] = lmax > kLamEasy;
+    stiff[j] = lmax > lam_easy<Q>();
     xl = fmaxf(xl, stiff[j] ? 0.0f : 2.0f * lmax);
   }
   // the warp's largest 2 max(W dt) (non-negative floats order like their
@@ -197,12 +209,12 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
   const int Rw = __popc(__ballot_sync(kFull, xw > thr_lane));
   float dne[Q];
   int nlo[Q], nhi[Q];
-  // u = (dt A)^k v unnormalized (|dt A| <= 2 kLamEasy keeps it small);
+  // u = (dt A)^k v unnormalized (|dt A| <= 2 lam_easy keeps it small);
   // inc = sum_k u / k!.  The term loop is outermost so that the Q cells'
   // recurrences interleave.  Slots past a cell's window start from whatever
   // the stage holds there: their rates and the rate into them are zero, so
   // their u is zero after one term and their inc stays zero.  Stiff cells
-  // run with rates above kLamEasy; their inc is never read.
+  // run with rates above lam_easy; their inc is never read.
   float u[Q][WM], inc[Q][WM];
 #pragma unroll
   for (int j = 0; j < Q; ++j) {

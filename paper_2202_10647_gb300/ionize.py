@@ -573,8 +573,9 @@ def counters(ws: torch.Tensor):
 
 
 def stiff_cells(ws: torch.Tensor) -> int:
-    """Cells of the last FP32 step that used `ws` with some W dt > 1,
-    finished on the long path; synchronizes."""
+    """Cells of the last FP32 step that used `ws` with some W dt > 1 (> 1.5
+    under a launch shape of one cell per lane), finished on the long path;
+    synchronizes."""
     return int(ws[8:12].cpu().view(torch.int32)[0])
 
 

@@ -157,3 +157,67 @@ def test_single_species_kernel_equals_general_kernel(shape, name):
     check(dict(N=Na.double().cpu().numpy(), lo=la.cpu().numpy(), hi=ha.cpu().numpy(),
                dne=da.double().cpu().numpy()), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F32,
           sd=wl.species, E=wl.E.double().numpy())
+
+
+def fields_at_top_rate(sd, lo, hi, target, dt=0.05):
+    """|E| per cell at which the largest rate of its window has W dt = target:
+    the lowest field on a grid in log |E| where it exceeds the target, then
+    bisection on the oracle's rates (Eq. 1 peaks and falls again at high
+    fields, so the grid picks the rising side)."""
+    osp = oracle_species(sd)
+    n = lo.shape[0]
+
+    def top(logE):
+        Wr = oracle.rates(osp, 10.0 ** logE, 0, sd.Z) * dt
+        k = np.arange(sd.Z)[:, None]
+        inwin = (k >= lo[None, :]) & (k < hi[None, :])
+        return np.where(inwin, Wr, 0.0).max(axis=0)
+
+    grid = np.arange(0.0, 6.0001, 0.05)  # log10 |E| in GV/m
+    above = np.stack([top(np.full(n, g)) > target for g in grid])
+    assert not above[0].any() and above.any(axis=0).all()
+    i = above.argmax(axis=0)
+    a, b = grid[i - 1], grid[i]
+    for _ in range(60):
+        m = 0.5 * (a + b)
+        up = top(m) > target
+        b, a = np.where(up, m, b), np.where(up, a, m)
+    E = (10.0 ** b).astype(np.float32)
+    got = top(np.log10(E.astype(np.float64)))
+    assert np.all(np.abs(got / target - 1.0) < 1e-4)
+    return E
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_series_bound_by_cells_per_lane(general):
+    """Cells whose largest window rate has 1 < W dt < 1.5 are finished by
+    the Taylor series in the streaming kernel when a lane holds one cell (a
+    warp's series then serves 32 cells) and become records for the Bateman
+    form when it holds two; both match the oracle.  `general` launches two
+    species at once (the general streaming kernel), otherwise one (the
+    single-species kernel)."""
+    dev = "cuda"
+    rng = np.random.default_rng(53)
+    wls = []
+    for sd, n, seed in ((W.nitrogen(), 2053, 54), (W.argon_like(), 3001, 55)):
+        wl = W.ladder_cells(sd, n, seed, block=64)
+        target = rng.uniform(1.02, 1.48, n)
+        wl.E.copy_(torch.from_numpy(fields_at_top_rate(sd, wl.lo.numpy().astype(int),
+                                                       wl.hi.numpy().astype(int), target)))
+        wls.append(wl)
+    groups = [wls] if general else [[wl] for wl in wls]
+    for shape, q in (((1, 8, 0), 1), ((2, 8, 0), 2)):
+        for group in groups:
+            jobs = []
+            for wl in group:
+                sp = ionize.Species(wl.species.U, wl.species.l, wl.species.m)
+                jobs.append((sp, wl.E.to(dev), wl.N.to(dev), wl.lo.clone().to(dev),
+                             wl.hi.clone().to(dev), torch.full((wl.ncells,), 9.0, device=dev)))
+            ws = ionize.step_batched(jobs, 0.05, shape=shape)
+            torch.cuda.synchronize()
+            tails = sum(wl.ncells % (32 * q) for wl in group)
+            want = tails if q == 1 else sum(wl.ncells for wl in group)
+            assert ionize.stiff_cells(ws) == want, (shape, ionize.stiff_cells(ws), want)
+            for wl, job in zip(group, jobs):
+                check(gpu_out(job), oracle_of(wl), wl.lo, wl.hi, ionize.ION_F32,
+                      sd=wl.species, E=wl.E.double().numpy())
