@@ -555,12 +555,13 @@ def main():
         t_plain4 = t4(lambda: ionize.step(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4),
                       reps4)
         t_net4 = t4(lambda: net4.step(wl4.E, wl4.N, wl4.lo, wl4.hi, 0.05, dne4, ws=ws4), reps4)
+        n_net4, n_plain4, tmo4 = ionize.surrogate_counters(ws4)
         # the same plain step with the launch shape the library's autotuner
-        # picks for these cells (the autotuner steps the arrays: restored by t4)
+        # picks for these cells (the autotuner steps the arrays: restored by t4;
+        # after the surrogate counters are read: it reuses their workspace)
         job4 = [(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, dne4)]
         shape4, _ = ionize.autotune(job4, 0.05, ws=ws4, reps=3)
         t_tuned4 = t4(lambda: ionize.step_batched(job4, 0.05, ws=ws4, shape=shape4), reps4)
-        n_net4, n_plain4, tmo4 = ionize.surrogate_counters(ws4)
         acc4 = None
         if rank == 0:
             import oracle
