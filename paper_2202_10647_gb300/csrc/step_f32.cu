@@ -156,6 +156,56 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 template <int Q>
 using PlaneRows = typename VecOf<Q>::T[ION_MAX_WINDOW][32];
 
+// The records of a warp's chunk: the stiff cells of all its lanes, one
+// atomic per class (narrow from the front of the arrays, wide from the
+// back) for the whole warp, cell j of every lane after cell j-1 of every
+// lane; the inputs as loaded (the stage's planes).
+template <int Q>
+__device__ __forceinline__ void append_records(const Scratch& S, int job, int c0,
+                                               const float (&Ec)[Q], const int (&lo)[Q],
+                                               const int (&hi)[Q], const bool (&take)[Q],
+                                               const PlaneRows<Q>& P, int lane) {
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) any = any || take[j];
+  if (!__ballot_sync(kFull, any)) return;
+  unsigned mn[Q], mw[Q], nn = 0, nw = 0;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    const bool wide = hi[j] - lo[j] + 1 > kRecNarrow;
+    mn[j] = __ballot_sync(kFull, take[j] && !wide);
+    mw[j] = __ballot_sync(kFull, take[j] && wide);
+    nn += __popc(mn[j]);
+    nw += __popc(mw[j]);
+  }
+  unsigned bn = 0, bw = 0;
+  if (lane == 0) {
+    if (nn) bn = atomicAdd(&S.hdr[kHdrRecNarrow], nn);
+    if (nw) bw = atomicAdd(&S.hdr[kHdrRecWide], nw);
+  }
+  bn = __shfl_sync(kFull, bn, 0);
+  bw = __shfl_sync(kFull, bw, 0);
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    if (take[j]) {
+      const bool wide = hi[j] - lo[j] + 1 > kRecNarrow;
+      const unsigned i = wide ? (unsigned)S.rec_cap - 1u - (bw + __popc(mw[j] & below))
+                              : bn + __popc(mn[j] & below);
+      S.rec_c[i] = (uint32_t)(c0 + j);
+      S.rec_job[i] = (uint8_t)job;
+      S.rec_E[i] = Ec[j];
+      S.rec_lohi[i] = (uint16_t)(lo[j] | (hi[j] << 8));
+      const int w = hi[j] - lo[j] + 1;
+#pragma unroll
+      for (int r = 0; r < ION_MAX_WINDOW; ++r)
+        if (r < w) S.rec_V[(int64_t)r * S.rec_cap + i] = vget(P[r][lane], j);
+    }
+    bn += __popc(mn[j]);
+    bw += __popc(mw[j]);
+  }
+}
+
 // CONS (the call has ION_CONSERVATION_CHECK; a separate instantiation, so
 // that the other calls carry none of it): cmax becomes the larger of itself
 // and the bits of |sum_r v'_r - sum_r v_r| of each cell finished here.
@@ -621,18 +671,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
                                      thr_lane, cmax);
     }
     // stiff cells: their inputs (as loaded) go to the record queue
-    bool any = false;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) any = any || stiff[j];
-    if (__ballot_sync(kFull, any)) {
-#pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        float vin[ION_MAX_WINDOW];
-#pragma unroll
-        for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = vget(st.P[r][lane], j);
-        append_record(a.ws, stiff[j], jid, c0 + j, Ev[j], lo[j], hi[j], vin);
-      }
-    }
+    append_records<Q>(a.ws, jid, c0, Ev, lo, hi, stiff, st.P, lane);
     __syncwarp();
   }
   cp_async_wait<0>();
@@ -898,18 +937,7 @@ __global__ void __maxnreg__(stream_regs<Q>())
         easy_cells<Q, 6, false, CONS>(J, a.pol, tab, st.P, lane, c0, Ev, lo, hi, ok, uni,
                                        stiff, thr_lane, cmax);
       // stiff cells: their inputs (as loaded) go to the record queue
-      bool any = false;
-#pragma unroll
-      for (int j = 0; j < Q; ++j) any = any || stiff[j];
-      if (__ballot_sync(kFull, any)) {
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-          float vin[ION_MAX_WINDOW];
-#pragma unroll
-          for (int r = 0; r < ION_MAX_WINDOW; ++r) vin[r] = vget(st.P[r][lane], j);
-          append_record(a.ws, stiff[j], 0, c0 + j, Ev[j], lo[j], hi[j], vin);
-        }
-      }
+      append_records<Q>(a.ws, 0, c0, Ev, lo, hi, stiff, st.P, lane);
     }
     __syncwarp();
   }
