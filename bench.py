@@ -86,10 +86,21 @@ def _recorded(path):
     return kv
 
 
+def recorded_issue_shape():
+    """The launch shape (cells per lane, warps per block, blocks per SM) the
+    committed instruction counts of the batched step were captured with."""
+    kv = _recorded(ISSUE_FILE)
+    try:
+        return tuple(int(x) for x in kv["shape"].split(","))
+    except (TypeError, KeyError, ValueError):
+        return None
+
+
 def batched_issue_roofline(ms, sm_mhz, num_sms):
     """Issue roofline of the batched step: the warp instructions of one step
-    (committed ncu record) against 4 warp instructions per SM cycle at the
-    SM clock sampled during the run, and each kernel's share."""
+    (committed ncu record, in the launch shape it was captured with; `ms` is
+    the step's time in that shape) against 4 warp instructions per SM cycle
+    at the SM clock sampled during the run, and each kernel's share."""
     kv = _recorded(ISSUE_FILE)
     if kv is None or not sm_mhz:
         return None
@@ -110,7 +121,8 @@ def batched_issue_roofline(ms, sm_mhz, num_sms):
             "issue_frac_in_capture": ki / (kus * 1e-6) / peak if kus > 0 else None}
     return {"bound": "issue", "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "G warp instructions/s", "frac": achieved / peak,
-            "warp_inst_per_step": inst, "kernels": kernels,
+            "warp_inst_per_step": inst, "kernels": kernels, "ms_per_step": ms,
+            "launch_shape": list(recorded_issue_shape() or ()),
             "record": os.path.relpath(ISSUE_FILE, ROOT)}
 
 
@@ -486,6 +498,24 @@ def main():
                 bt.append((a_, b_))
         torch.cuda.synchronize()
         bms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in bt]))
+        # the step again in the shape of the committed instruction counts
+        # (the issue roofline's), when the autotuner picked another
+        rshape = recorded_issue_shape()
+        bms_rec = bms
+        if rshape and rshape != (shape.cells_per_lane, shape.warps_per_block,
+                                 shape.blocks_per_sm):
+            bt = []
+            for s_ in range(3 + max(5, args.steps // 5)):
+                brestore()
+                a_ = torch.cuda.Event(enable_timing=True)
+                b_ = torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                ionize.step_batched(bjobs, 0.05, ws=bws, shape=rshape)
+                b_.record(stream)
+                if s_ >= 3:
+                    bt.append((a_, b_))
+            torch.cuda.synchronize()
+            bms_rec = float(np.mean([a_.elapsed_time(b_) for a_, b_ in bt]))
         bcells = sum(w_.ncells for w_ in bjobs_wl)
         bbytes = sum(int(W.window_bytes_per_cell(l0, h0).sum()) for (_, l0, h0) in pristine)
         # accuracy on sampled cells of each species
@@ -512,7 +542,8 @@ def main():
                    "launch_shape": {"cells_per_lane": shape.cells_per_lane,
                                     "warps_per_block": shape.warps_per_block,
                                     "blocks_per_sm": shape.blocks_per_sm},
-                   "max_abs_err_N_vs_oracle": bacc}
+                   "max_abs_err_N_vs_oracle": bacc,
+                   "ms_per_step_at_recorded_shape": bms_rec}
         del bjobs, bjobs_wl, pristine, bws
 
     # -- surrogate form: Ar-like cells, rates from the tensor-core network ----
@@ -824,7 +855,7 @@ def main():
     clocks = clk.summary()
     if batched is not None:
         batched["roofline"] = batched_issue_roofline(
-            batched["ms_per_step"], clocks.get("sm_mhz") or clocks.get("sm_max_mhz"),
+            batched["ms_per_step_at_recorded_shape"], clocks.get("sm_mhz") or clocks.get("sm_max_mhz"),
             torch.cuda.get_device_properties(dev).multi_processor_count)
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,

@@ -19,6 +19,7 @@ def write_record(path, sha, inst=4000, scale=2):
         f.write("stream_warp_inst: 1000\nstiff_warp_inst: 900\nfb_warp_inst: 100\n")
         f.write("stream_us: 1.0\nstiff_us: 2.0\nfb_us: 0.5\n")
         f.write(f"warp_inst_per_step: {inst}\n")
+        f.write("shape: 1,8,0\n")
 
 
 def test_issue_roofline_from_a_current_record(tmp_path, monkeypatch):
@@ -31,6 +32,7 @@ def test_issue_roofline_from_a_current_record(tmp_path, monkeypatch):
     assert r["achieved"] == pytest.approx(4.0)  # G warp instructions / s
     assert r["peak"] == pytest.approx(8.0)
     assert r["frac"] == pytest.approx(0.5)
+    assert r["launch_shape"] == [1, 8, 0] and bench.recorded_issue_shape() == (1, 8, 0)
     k = r["kernels"]["ion_stiff_kernel"]
     assert k["warp_inst_per_step"] == pytest.approx(1800)
     assert k["issue_frac_in_capture"] == pytest.approx(900 / 2e-6 / 8e9)
@@ -41,6 +43,7 @@ def test_stale_records_are_not_used(tmp_path, monkeypatch):
     write_record(p, "0" * 64)
     monkeypatch.setattr(bench, "ISSUE_FILE", str(p))
     assert bench.batched_issue_roofline(ms=1.0, sm_mhz=2000.0, num_sms=152) is None
+    assert bench.recorded_issue_shape() is None
     t = tmp_path / "traffic.txt"
     t.write_text("sources_sha256: " + "0" * 64 + "\ndram_bytes_per_step: 123\n")
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(t))
