@@ -199,7 +199,7 @@ __device__ __forceinline__ bool update_cell(const JobIO& J, const Policy& pol, i
       } else {
         if (allow_fb && (pol.flags & ION_NO_FP64_FALLBACK) == 0 &&
             ((pol.flags & ION_FORCE_FP64_COEF) != 0 ||
-             (pol.gap > 0.0 && near_degenerate<T, WM>(lam, w, pol_gap<T>(pol)))))
+             (pol_gap<T>(pol) > T(0) && near_degenerate<T, WM>(lam, w, pol_gap<T>(pol)))))
           return true;
         dne = dd_update<T, WM>(v, lam, w);
       }
