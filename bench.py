@@ -821,23 +821,26 @@ def main():
                     ionize.copy_cells(odne, dne, c0, c1 - c0)
             stream.wait_stream(sD)
 
-        ke = max(3, min(10, args.steps // 20))
+        ke = max(5, min(20, args.steps // 15))
 
+        # each step timed on its own; the median, since the host link is
+        # shared with the machine's other GPUs and their jobs' copies
         def e2e_time(fn):
             for _ in range(2):
                 fn()
             torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(ke):
+            ev_ = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(ke)]
+            for a, b in ev_:
+                a.record(stream)
                 fn()
-            b.record(stream)
+                b.record(stream)
             torch.cuda.synchronize()
-            return a.elapsed_time(b) / ke
+            t_ = [a.elapsed_time(b) for a, b in ev_]
+            return float(np.median(t_)), float(np.min(t_)), float(np.max(t_))
 
-        e_seq_ms = e2e_time(e2e_sequential)
-        e_ms = e2e_time(e2e_pipelined)
+        e_seq_ms, e_seq_min, e_seq_max = e2e_time(e2e_sequential)
+        e_ms, e_min, e_max = e2e_time(e2e_pipelined)
         # the pipelined run's outputs are those of one whole-grid step
         e2e_sequential()
         torch.cuda.synchronize()
@@ -853,7 +856,8 @@ def main():
                "how": f"{nch} cell chunks, host-to-device, step and device-to-host on three "
                       "streams (pinned host buffers; ion_copy_cells moves all planes of a "
                       "chunk in one strided copy)",
-               "sequential_ms_per_step": e_seq_ms,
+               "steps_timed": ke, "ms_min_max": [e_min, e_max],
+               "sequential_ms_per_step": e_seq_ms, "sequential_ms_min_max": [e_seq_min, e_seq_max],
                "pipelined_output_equals_sequential": e2e_same}
         del hE, hN, oN
 
