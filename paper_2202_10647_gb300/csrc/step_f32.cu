@@ -146,11 +146,14 @@ __device__ __forceinline__ int job_of(const BatchArgs& a, int g) {
 // Easy path of the lane's Q cells (c0..c0+Q-1 of job J, window bound WM).
 // Every lane of the warp calls this.  Cells whose rates all have
 // W dt <= lam_easy<Q>() are finished; stiff[j] marks the others, left untouched.
-// Every window rate first takes the plain FP32 exponent y = (a_hi + a_lo) -
-// b log2|E| - C/|E|: its error is below ~6e-5 in log2 units even for terms of
-// 10^3, i.e. a relative error of W dt below 4e-5, which moves populations by
-// at most 4e-5 W dt; rates above kLamPrecise = 2^-6 (where that could reach
-// 6e-7) are recomputed in float-float.  The Taylor series runs the warp's
+// Every window rate first takes the plain FP32 exponent y = a_hi - b log2|E|
+// - C/|E| (a_lo, the low part of a, left out: half an ulp of a, below 1e-5 in
+// log2 units for |a| < 256): its error is below ~7e-5 in log2 units even for
+// terms of 10^3, i.e. a relative error of W dt below 5e-5, which moves
+// populations by at most 5e-5 W dt; rates above kLamPrecise = 2^-6 (where
+// that could reach 8e-7) are recomputed in float-float.  Past the cutoff
+// (C/|E| > kCutoffLog2, where Eq. 1 is 0) y lies far below -126, so the
+// SFU's ex2, which flushes results below 2^-126 to 0, needs no test for it.  The Taylor series runs the warp's
 // largest term count (extra terms only add accuracy), counted by one ballot:
 // lane i holds thr_lane = kThrF32[i] (infinity from lane kEasyTerms on).
 template <int Q>
@@ -239,9 +242,8 @@ __device__ __forceinline__ void easy_cells(const JobIO& J, const Policy& pol,
 #pragma unroll
     for (int r = 0; r < WM - 1; ++r) {
       const float4 h = tab.hi[base + r];  // < ION_MAX_Z + ION_MAX_WINDOW
-      const float q = h.z * f.rE;
-      const float y = (fmaf(-h.y, f.lg, h.x) - q) + h.w;
-      const bool on = live && r < w[j] - 1 && q <= (float)kCutoffLog2;
+      const float y = fmaf(-h.z, f.rE, fmaf(-h.y, f.lg, h.x));
+      const bool on = live && r < w[j] - 1;
       lam[j][r] = on ? ex2_approx(fminf(y, 99.0f)) : 0.0f;
     }
 #pragma unroll
