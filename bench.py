@@ -615,13 +615,16 @@ def main():
         # the same plain step with the launch shape the library's autotuner
         # picks for these cells (the autotuner steps the arrays: restored by t4;
         # after the surrogate counters are read: it reuses their workspace)
-        # (its pick and one cell per lane timed again from the restored state,
-        # the faster kept: the autotuner's launches step the arrays in turn)
+        # (its pick and the two default shapes timed again from the restored
+        # state, the fastest kept: the autotuner's launches step the arrays in
+        # turn)
         job4 = [(sp4, wl4.E, wl4.N, wl4.lo, wl4.hi, dne4)]
         shape4, _ = ionize.autotune(job4, 0.05, ws=ws4, reps=3)
         t_tuned4 = t4(lambda: ionize.step_batched(job4, 0.05, ws=ws4, shape=shape4), reps4)
-        alt4 = ionize.LaunchShape(1, 8, 0)
-        if (shape4.cells_per_lane, shape4.warps_per_block, shape4.blocks_per_sm) != (1, 8, 0):
+        for c4 in ((1, 8, 0), (2, 8, 0)):
+            if (shape4.cells_per_lane, shape4.warps_per_block, shape4.blocks_per_sm) == c4:
+                continue
+            alt4 = ionize.LaunchShape(*c4)
             t_alt4 = t4(lambda: ionize.step_batched(job4, 0.05, ws=ws4, shape=alt4), reps4)
             if t_alt4 < t_tuned4:
                 shape4, t_tuned4 = alt4, t_alt4
