@@ -282,7 +282,10 @@ ION_API int ion_step_batched(const ion_batch_job* jobs, int njobs, double dt_fs,
  * built launch shape (cells per lane x warps per block x blocks per SM) and
  * returns the shape with the smallest median time over `reps` (1..64) timed
  * steps, and that time in ms (best_ms may be NULL).  It runs real steps on
- * the jobs' arrays, so pass copies of the state.  It creates CUDA events and
+ * the jobs' arrays, so pass copies of the state.  The steps run one after
+ * another on the same arrays, so where windows slide each shape is timed on
+ * a later state than the one before it: time the chosen shape (and the
+ * default) again from the state that matters.  It creates CUDA events and
  * synchronizes on them: call it outside any stream capture.  Errors: those
  * of ion_step_batched, ION_EINVAL for ION_F64_PLAIN or a bad reps. */
 ION_API int ion_autotune(const ion_batch_job* jobs, int njobs, double dt_fs,
